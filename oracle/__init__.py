@@ -1,0 +1,245 @@
+"""FP64 CPU oracle for the finite-difference GPE step on a sampled grid.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never calls it and shares no code with it.
+
+The arithmetic lives in ``gpe_oracle.c`` (plain loops, FP64, OpenMP across
+cells only); this module compiles it with gcc on first use and wraps it with
+numpy arrays.  Paper: "Efficient simulation of Bose-Einstein condensates in
+nontrivial topologies", Sec. II A (general algorithm), Eqs. (3), (5)-(9).
+
+Conventions: a dense box array has numpy shape (nz, ny, nx) (x fastest), so a
+cell's linear index is ``i + nx*(j + ny*k)``.  The active cells of a grid are
+kept in ascending linear order; a compact vector holds one value per active
+cell in that order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gpe_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libgpe_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libgpe_oracle.so`` with gcc."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.orc_neighbors.restype = ctypes.c_int
+        lib.orc_neighbors.argtypes = [ctypes.c_int64, _c_i64p, ctypes.c_int64,
+                                      ctypes.c_int64, ctypes.c_int64, _c_i64p]
+        lib.orc_laplacian.restype = None
+        lib.orc_laplacian.argtypes = [ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3 + [_c_f64p, _c_f64p]
+        lib.orc_rhs_real.restype = None
+        lib.orc_rhs_real.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
+                                     + [_c_f64p, ctypes.c_double, _c_f64p, _c_f64p])
+        lib.orc_rk4_step.restype = ctypes.c_int
+        lib.orc_rk4_step.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
+                                     + [_c_f64p, _c_f64p, ctypes.c_int, _c_f64p]
+                                     + [ctypes.c_double] * 4 + [_c_f64p])
+        lib.orc_itp_step.restype = ctypes.c_double
+        lib.orc_itp_step.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
+                                     + [_c_f64p] + [ctypes.c_double] * 3 + [_c_f64p])
+        lib.orc_observables.restype = None
+        lib.orc_observables.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
+                                        + [_c_f64p, ctypes.c_double, _c_f64p, _c_f64p])
+        lib.orc_overlap.restype = None
+        lib.orc_overlap.argtypes = [ctypes.c_int64, _c_f64p, _c_f64p, ctypes.c_double, _c_f64p]
+        lib.orc_tf_mu.restype = ctypes.c_double
+        lib.orc_tf_mu.argtypes = [ctypes.c_int64, _c_f64p] + [ctypes.c_double] * 3
+        lib.orc_ramp_s.restype = ctypes.c_double
+        lib.orc_ramp_s.argtypes = [ctypes.c_int, _c_f64p, ctypes.c_double, ctypes.c_double]
+        lib.orc_rk4_adjoint_step.restype = ctypes.c_int
+        lib.orc_rk4_adjoint_step.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
+                                             + [_c_f64p, _c_f64p, ctypes.c_int, _c_f64p]
+                                             + [ctypes.c_double] * 4 + [_c_f64p, _c_f64p, _c_f64p])
+        _lib = lib
+        return lib
+
+
+def _p64(a):
+    return a.ctypes.data_as(_c_f64p) if a is not None else None
+
+
+def _pi64(a):
+    return a.ctypes.data_as(_c_i64p)
+
+
+def _cvec(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a, a.view(np.float64).ctypes.data_as(_c_f64p)
+
+
+class Grid:
+    """The discrete problem of Sec. II A: a box, its spacings and the active set.
+
+    ``mask`` is a boolean array of shape (nz, ny, nx).  Cells outside the mask
+    are deleted from the Laplacian (psi == 0 there, never updated).
+    """
+
+    def __init__(self, mask: np.ndarray, h):
+        mask = np.asarray(mask, dtype=bool)
+        assert mask.ndim == 3
+        self.nz, self.ny, self.nx = mask.shape
+        self.h = tuple(float(x) for x in (h if np.ndim(h) else (h, h, h)))
+        self.dV = self.h[0] * self.h[1] * self.h[2]
+        self.mask = mask
+        self.cells = np.flatnonzero(mask.ravel()).astype(np.int64)
+        self.n = int(self.cells.size)
+        self.nbr = np.empty((self.n, 6), dtype=np.int64)
+        rc = _load().orc_neighbors(self.n, _pi64(self.cells), self.nx, self.ny,
+                                   self.nz, _pi64(self.nbr))
+        assert rc == 0
+
+    # --- dense <-> compact ------------------------------------------------
+    def compact(self, dense: np.ndarray) -> np.ndarray:
+        return np.ascontiguousarray(np.asarray(dense).ravel()[self.cells])
+
+    def dense(self, vec: np.ndarray, dtype=None) -> np.ndarray:
+        vec = np.asarray(vec)
+        out = np.zeros(self.nx * self.ny * self.nz, dtype=dtype or vec.dtype)
+        out[self.cells] = vec
+        return out.reshape(self.nz, self.ny, self.nx)
+
+    def ijk(self) -> np.ndarray:
+        c = self.cells
+        return np.stack([c % self.nx, (c // self.nx) % self.ny, c // (self.nx * self.ny)], axis=1)
+
+
+def laplacian(grid: Grid, psi: np.ndarray) -> np.ndarray:
+    psi, pp = _cvec(psi)
+    out = np.empty(grid.n, dtype=np.complex128)
+    _load().orc_laplacian(grid.n, _pi64(grid.nbr), *grid.h, pp, out.view(np.float64).ctypes.data_as(_c_f64p))
+    return out
+
+
+def rhs_real(grid: Grid, V: np.ndarray, g: float, y: np.ndarray) -> np.ndarray:
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    y, yp = _cvec(y)
+    out = np.empty(grid.n, dtype=np.complex128)
+    _load().orc_rhs_real(grid.n, _pi64(grid.nbr), *grid.h, _p64(V), float(g), yp,
+                         out.view(np.float64).ctypes.data_as(_c_f64p))
+    return out
+
+
+def _ramp_args(V1, knots, T):
+    if V1 is None or knots is None:
+        return None, 0, None, 0.0
+    V1 = np.ascontiguousarray(V1, dtype=np.float64)
+    knots = np.ascontiguousarray(knots, dtype=np.float64)
+    return V1, int(knots.size), knots, float(T)
+
+
+def rk4_step(grid: Grid, V0, psi, g, t, dt, V1=None, knots=None, T=0.0) -> np.ndarray:
+    """One classic RK4 step (Butcher form) of Eq. (8); returns the new psi."""
+    V0 = np.ascontiguousarray(V0, dtype=np.float64)
+    V1, nk, kn, T = _ramp_args(V1, knots, T)
+    y = np.array(psi, dtype=np.complex128, copy=True)
+    rc = _load().orc_rk4_step(grid.n, _pi64(grid.nbr), *grid.h, _p64(V0), _p64(V1), nk,
+                              _p64(kn), T, float(g), float(t), float(dt),
+                              y.view(np.float64).ctypes.data_as(_c_f64p))
+    assert rc == 0
+    return y
+
+
+def itp_step(grid: Grid, V, psi, g, dt, N=1.0):
+    """One imaginary-time split step with renormalisation (Eqs. (6)-(7)).
+
+    Returns (new psi, norm before renormalisation)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    y = np.array(psi, dtype=np.complex128, copy=True)
+    nrm = _load().orc_itp_step(grid.n, _pi64(grid.nbr), *grid.h, _p64(V), float(g), float(dt),
+                               float(N), y.view(np.float64).ctypes.data_as(_c_f64p))
+    return y, nrm
+
+
+def observables(grid: Grid, V, g, psi) -> dict:
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    psi, pp = _cvec(psi)
+    out = np.zeros(7)
+    _load().orc_observables(grid.n, _pi64(grid.nbr), *grid.h, _p64(V), float(g), pp, _p64(out))
+    return dict(norm=out[0], energy=out[1], mu=out[2], nonfinite=int(out[3]),
+                e_kin=out[4], e_pot=out[5], e_int=out[6])
+
+
+def overlap(a, b, dV) -> complex:
+    a, ap = _cvec(a)
+    b, bp = _cvec(b)
+    out = np.zeros(2)
+    _load().orc_overlap(a.size, ap, bp, float(dV), _p64(out))
+    return complex(out[0], out[1])
+
+
+def tf_mu(V, dV, g, N) -> float:
+    """Thomas-Fermi chemical potential of Eq. (5) for atom number N."""
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).ravel())
+    return float(_load().orc_tf_mu(V.size, _p64(V), float(dV), float(g), float(N)))
+
+
+def ramp_s(knots, T, t) -> float:
+    knots = np.ascontiguousarray(knots, dtype=np.float64)
+    return float(_load().orc_ramp_s(knots.size, _p64(knots), float(T), float(t)))
+
+
+def rk4_adjoint_step(grid: Grid, V0, V1, knots, T, g, t, dt, y0, lam):
+    """Reverse one RK4 step: returns (dL/dy0, dL/dknots contribution)."""
+    V0 = np.ascontiguousarray(V0, dtype=np.float64)
+    V1, nk, kn, T = _ramp_args(V1, knots, T)
+    y0, yp = _cvec(y0)
+    lam = np.array(lam, dtype=np.complex128, copy=True)
+    grad = np.zeros(max(nk, 1))
+    rc = _load().orc_rk4_adjoint_step(grid.n, _pi64(grid.nbr), *grid.h, _p64(V0), _p64(V1), nk,
+                                      _p64(kn), T, float(g), float(t), float(dt), yp,
+                                      lam.view(np.float64).ctypes.data_as(_c_f64p), _p64(grad))
+    assert rc == 0
+    return lam, grad[:nk]
+
+
+def ramp_loss_and_grad(grid: Grid, V0, V1, knots, T, g, dt, nsteps, psi0, psi_target, t0=0.0):
+    """Infidelity L = 1 - |<psi_t|psi(T)>|^2 after nsteps RK4 steps, and dL/dknots.
+
+    Forward: store every step's start state (small grids only); backward: the
+    step adjoint in reverse order.  The loss gradient seed is
+    dL/dpsi = -2 c psi_t dV with c = <psi_t|psi(T)>.
+    """
+    states = [np.array(psi0, dtype=np.complex128)]
+    y = states[0]
+    for s in range(nsteps):
+        y = rk4_step(grid, V0, y, g, t0 + s * dt, dt, V1, knots, T)
+        states.append(y)
+    c = overlap(psi_target, y, grid.dV)
+    loss = 1.0 - abs(c) ** 2
+    lam = -2.0 * c * np.asarray(psi_target, dtype=np.complex128) * grid.dV
+    grad = np.zeros(len(knots))
+    for s in reversed(range(nsteps)):
+        lam, gk = rk4_adjoint_step(grid, V0, V1, knots, T, g, t0 + s * dt, dt, states[s], lam)
+        grad += gk
+    return loss, grad, y

@@ -1,0 +1,452 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a library
+construction of the paper's own definition (Kronecker-sum Laplacian with rows
+and columns deleted, Sec. II A), closed forms, dense matrix functions on tiny
+grids, conservation laws, the paper's printed App. A tables, and finite
+differences.  A plausible slip in the oracle (dropped term, wrong sign or
+factor, wrong stage time, transposed index) fails at least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+from scipy.sparse.linalg import eigsh
+
+from paper_2603_05447_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def kron_laplacian(nx, ny, nz, h):
+    """Sec. II A: the Cartesian 7-point Laplacian built from Kronecker products
+    of identities and the tridiagonal [1, -2, 1]/h^2 (x fastest)."""
+    def d2(n, hh):
+        return sp.diags([np.ones(n - 1), -2 * np.ones(n), np.ones(n - 1)], [-1, 0, 1]) / hh ** 2
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    return (sp.kron(Iz, sp.kron(Iy, d2(nx, h[0]))) + sp.kron(Iz, sp.kron(d2(ny, h[1]), Ix))
+            + sp.kron(d2(nz, h[2]), sp.kron(Iy, Ix))).tocsr()
+
+
+def reduced_laplacian(grid, h):
+    """Rows and columns of inactive cells deleted (Sec. II A)."""
+    L = kron_laplacian(grid.nx, grid.ny, grid.nz, h)
+    return L[grid.cells][:, grid.cells]
+
+
+def random_mask(shape, frac, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(size=shape) < frac
+
+
+def cvec(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+# ----------------------------------------------------------------- grid
+def test_neighbors_symmetric_and_match_dense_roll(oracle_mod):
+    mask = random_mask((7, 6, 9), 0.6, 11)
+    g = oracle_mod.Grid(mask, (0.3, 0.4, 0.5))
+    pos = -np.ones(mask.size, dtype=np.int64)
+    pos[g.cells] = np.arange(g.n)
+    ijk = g.ijk()
+    for e, (dx, dy, dz) in enumerate([(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]):
+        i, j, k = ijk[:, 0] + dx, ijk[:, 1] + dy, ijk[:, 2] + dz
+        inside = (i >= 0) & (i < g.nx) & (j >= 0) & (j < g.ny) & (k >= 0) & (k < g.nz)
+        want = np.full(g.n, -1, dtype=np.int64)
+        lin = (i + g.nx * (j + g.ny * k))[inside]
+        want[inside] = pos[lin]
+        assert np.array_equal(g.nbr[:, e], want)
+        # symmetry: my +e neighbour has me as its -e neighbour
+        opp = e ^ 1
+        has = g.nbr[:, e] >= 0
+        assert np.array_equal(g.nbr[g.nbr[has, e], opp], np.flatnonzero(has))
+
+
+# ----------------------------------------------------------------- Laplacian
+@pytest.mark.parametrize("frac", [1.0, 0.55])
+def test_laplacian_equals_kronecker_sum_with_deleted_rows(oracle_mod, frac):
+    h = (0.21, 0.34, 0.47)                          # anisotropic spacings, App. B
+    mask = random_mask((9, 8, 10), frac, 3)
+    g = oracle_mod.Grid(mask, h)
+    L = reduced_laplacian(g, h)
+    psi = cvec(g.n, 5)
+    assert relerr(oracle_mod.laplacian(g, psi), L @ psi) < 1e-14
+
+
+def test_laplacian_all_active_equals_dense_zero_padded_fd(oracle_mod):
+    h = (0.25, 0.3, 0.2)
+    shape = (12, 10, 11)
+    g = oracle_mod.Grid(np.ones(shape, bool), h)
+    dense = cvec(np.prod(shape), 9).reshape(shape)
+    p = np.pad(dense, 1)
+    ref = ((p[1:-1, 1:-1, 2:] - 2 * dense + p[1:-1, 1:-1, :-2]) / h[0] ** 2
+           + (p[1:-1, 2:, 1:-1] - 2 * dense + p[1:-1, :-2, 1:-1]) / h[1] ** 2
+           + (p[2:, 1:-1, 1:-1] - 2 * dense + p[:-2, 1:-1, 1:-1]) / h[2] ** 2)
+    out = g.dense(oracle_mod.laplacian(g, g.compact(dense)))
+    assert relerr(out, ref) < 1e-14
+
+
+def test_laplacian_exact_on_quadratics_and_kills_constants(oracle_mod):
+    box = inputs.Box(10, 9, 8, 0.2, 0.3, 0.4)
+    mask = random_mask(box.shape, 0.8, 4)
+    g = oracle_mod.Grid(mask, (box.hx, box.hy, box.hz))
+    x, y, z = box.coords_of(g.ijk())
+    interior = np.all(g.nbr >= 0, axis=1)
+    assert interior.sum() > 20
+    q = (x * x + 2 * y * y + 3 * z * z).astype(np.complex128)
+    lap = oracle_mod.laplacian(g, q)
+    assert np.allclose(lap[interior], 12.0, rtol=0, atol=1e-10)
+    const = np.full(g.n, 2.5 - 1.5j)
+    assert np.allclose(oracle_mod.laplacian(g, const)[interior], 0.0, atol=1e-11)
+
+
+# ----------------------------------------------------------------- observables
+def ho_1d(n, h):
+    x = (np.arange(n) - (n - 1) / 2) * h
+    d = 1.0 / h ** 2 + 0.5 * x ** 2          # -1/2 [1,-2,1]/h^2 + x^2/2
+    e = -0.5 / h ** 2 * np.ones(n - 1)
+    w, v = sla.eigh_tridiagonal(d, e, select="i", select_range=(0, 0))
+    return w[0], v[:, 0]
+
+
+def test_harmonic_exact_discrete_ground_state_energy(oracle_mod):
+    """g = 0, 64^3, h = 0.25: the separable discrete ground state has
+    E = mu = 3 lambda_min(1D); it is 1.5 up to the O(h^2) discretisation error."""
+    n, h = 64, 0.25
+    lam, v = ho_1d(n, h)
+    assert abs(3 * lam - 1.4941174639) < 1e-9
+    box = inputs.cubic_box(n, h)
+    g = oracle_mod.Grid(np.ones(box.shape, bool), h)
+    psi = np.einsum("k,j,i->kji", v, v, v).astype(np.complex128) / math.sqrt(box.dV)
+    V = inputs.dense_potential(box, inputs.Harmonic())
+    obs = oracle_mod.observables(g, g.compact(V), 0.0, g.compact(psi))
+    assert abs(obs["norm"] - 1.0) < 1e-12
+    assert abs(obs["energy"] - 3 * lam) < 1e-11
+    assert abs(obs["mu"] - 3 * lam) < 1e-11
+    assert abs(obs["energy"] - 1.5) < 3 * h ** 2 / 32 * 1.01 + 1e-6   # stated discretisation error
+
+
+def test_observables_overlap_nonfinite_and_interaction(oracle_mod):
+    box = inputs.Box(6, 5, 7, 0.3, 0.3, 0.3)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.7, 2), 0.3)
+    psi = cvec(g.n, 3)
+    V = np.random.default_rng(4).uniform(0, 2, g.n)
+    o0 = oracle_mod.observables(g, V, 0.0, psi)
+    o1 = oracle_mod.observables(g, V, 3.0, psi)
+    rho = np.abs(psi) ** 2
+    # E(g) - E(0) = g/2 sum rho^2 dV and mu gains twice that per atom
+    assert abs((o1["energy"] - o0["energy"]) - 1.5 * np.sum(rho ** 2) * g.dV) < 1e-10
+    assert abs((o1["mu"] - o0["mu"]) * o1["norm"] - 3.0 * np.sum(rho ** 2) * g.dV) < 1e-10
+    assert abs(oracle_mod.overlap(psi, psi, g.dV) - o0["norm"]) < 1e-12
+    # kinetic energy is Re<psi, T psi> = <psi, T psi> (T symmetric): matches the sparse matrix
+    L = reduced_laplacian(g, g.h)
+    assert abs(o0["e_kin"] - np.real(np.vdot(psi, -0.5 * (L @ psi))) * g.dV) < 1e-10
+    bad = psi.copy()
+    bad[3] = np.nan
+    bad[7] = np.inf
+    assert oracle_mod.observables(g, V, 0.0, bad)["nonfinite"] == 2
+
+
+def test_tf_mu_harmonic_closed_form(oracle_mod):
+    """Eq. (5) in V = r^2/2: mu = 1/2 (15 g N / 4 pi)^(2/5)."""
+    g_, N = 500.0, 1.0
+    mu_exact = 0.5 * (15 * g_ * N / (4 * math.pi)) ** 0.4
+    box = inputs.cubic_box(96, 0.08)
+    V = inputs.dense_potential(box, inputs.Harmonic())
+    mu = oracle_mod.tf_mu(V, box.dV, g_, N)
+    assert abs(mu - mu_exact) / mu_exact < 2e-3
+    n = np.sum(np.maximum(mu - V, 0) / g_) * box.dV
+    assert abs(n - N) < 1e-9
+
+
+# ----------------------------------------------------------------- imaginary time
+def itp_matrix(g, V, dt):
+    """g = 0: the ITP step before renormalisation is D (I - dt/2 T)^2 D with
+    D = diag(exp(-V dt/2)) and T = -1/2 Laplacian (Sec. II A)."""
+    L = reduced_laplacian(g, g.h).toarray()
+    K = np.eye(g.n) - 0.5 * dt * (-0.5 * L)
+    D = np.diag(np.exp(-V * dt / 2))
+    return D @ K @ K @ D
+
+
+def test_itp_step_g0_equals_dense_linear_map(oracle_mod):
+    box = inputs.Box(8, 7, 6, 0.4, 0.45, 0.5)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.75, 8), g_h := (0.4, 0.45, 0.5))
+    V = np.random.default_rng(1).uniform(0, 3, g.n)
+    psi = cvec(g.n, 2)
+    dt, N = 0.02, 2.5
+    out, nrm = oracle_mod.itp_step(g, V, psi, 0.0, dt, N)
+    ref = itp_matrix(g, V, dt) @ psi
+    assert abs(nrm - np.sum(np.abs(ref) ** 2) * g.dV) / nrm < 1e-13
+    ref = ref * math.sqrt(N / (np.sum(np.abs(ref) ** 2) * g.dV))
+    assert relerr(out, ref) < 1e-13
+
+
+def test_itp_fixed_point_is_dominant_eigenvector(oracle_mod):
+    """Repeated ITP steps at g = 0 converge to the dominant eigenvector of the
+    step matrix, computed by ARPACK on the sparse Kronecker construction."""
+    n, h, dt = 14, 0.5, 0.02
+    box = inputs.cubic_box(n, h)
+    g = oracle_mod.Grid(np.ones(box.shape, bool), h)
+    V = g.compact(inputs.dense_potential(box, inputs.Harmonic()))
+    L = reduced_laplacian(g, g.h)
+    K = sp.identity(g.n) + 0.25 * dt * L
+    D = sp.diags(np.exp(-V * dt / 2))
+    A = (D @ K @ K @ D).tocsc()
+    w, vec = eigsh(A, k=1, which="LA", tol=1e-14)
+    vec = vec[:, 0] * np.sign(vec[:, 0].sum())
+    vec = vec / math.sqrt(np.sum(vec ** 2) * g.dV)
+    psi = g.compact(inputs.gaussian_with_noise(box, seed=1, noise=1e-3))
+    for _ in range(2500):
+        psi, _ = oracle_mod.itp_step(g, V, psi, 0.0, dt, 1.0)
+    phase = np.vdot(vec, psi) / abs(np.vdot(vec, psi))
+    assert relerr(psi / phase, vec) < 1e-8
+
+
+def test_itp_interacting_fixed_point_solves_stationary_gpe(oracle_mod):
+    """At g > 0 the ITP fixed point solves Eq. (1) on the grid up to a splitting
+    error that shrinks with dt; the discrete virial identity
+    2 E_kin - 2 E_pot + 3 E_int = 0 holds to O(h^2)."""
+    n, h, g_ = 24, 0.4, 30.0
+    box = inputs.cubic_box(n, h)
+    g = oracle_mod.Grid(np.ones(box.shape, bool), h)
+    V = g.compact(inputs.dense_potential(box, inputs.Harmonic()))
+    res = []
+    for dt in (0.004, 0.002):
+        psi = g.compact(inputs.gaussian_with_noise(box, seed=1, noise=0.0))
+        for _ in range(int(12.0 / dt)):
+            psi, _ = oracle_mod.itp_step(g, V, psi, g_, dt, 1.0)
+        obs = oracle_mod.observables(g, V, g_, psi)
+        Hpsi = -0.5 * oracle_mod.laplacian(g, psi) + (V + g_ * np.abs(psi) ** 2) * psi
+        res.append(np.linalg.norm(Hpsi - obs["mu"] * psi) / np.linalg.norm(psi))
+        vir = 2 * obs["e_kin"] - 2 * obs["e_pot"] + 3 * obs["e_int"]
+        assert abs(vir) / obs["energy"] < 0.02
+    assert res[0] < 0.05
+    assert 1.6 < res[0] / res[1] < 2.4      # first order in dt
+
+
+# ----------------------------------------------------------------- real time (RK4)
+def dense_H(g, V):
+    L = reduced_laplacian(g, g.h).toarray()
+    return -0.5 * L + np.diag(V)
+
+
+def test_rk4_step_g0_is_taylor_polynomial_of_propagator(oracle_mod):
+    """Static V, g = 0: one classic RK4 step is P4(-i H dt) psi with
+    P4(z) = 1 + z + z^2/2 + z^3/6 + z^4/24."""
+    box = inputs.Box(7, 8, 6, 0.3, 0.35, 0.4)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.7, 21), (0.3, 0.35, 0.4))
+    V = np.random.default_rng(3).uniform(0, 4, g.n)
+    psi = cvec(g.n, 4)
+    dt = 0.004
+    Z = -1j * dt * dense_H(g, V)
+    P = np.eye(g.n) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    out = oracle_mod.rk4_step(g, V, psi, 0.0, 0.0, dt)
+    assert relerr(out, P @ psi) < 1e-13
+
+
+def test_rk4_fourth_order_against_matrix_exponential_with_time_dependent_shift(oracle_mod):
+    """V(t) = V0 + s(t) (a uniform shift ramped by the knot schedule) commutes
+    with H, so the exact solution is exp(-i H t) psi exp(-i int s).  RK4 with
+    the right stage times c = (0, 1/2, 1/2, 1) converges at fourth order."""
+    box = inputs.Box(6, 6, 5, 0.35, 0.35, 0.35)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 5), 0.35)
+    V0 = np.random.default_rng(6).uniform(0, 2, g.n)
+    V1 = V0 + 1.0
+    knots = np.array([0.0, 3.0, -2.0, 1.0, 4.0])
+    T = 0.2
+    psi0 = cvec(g.n, 7)
+    H0 = dense_H(g, V0)
+    tt = np.linspace(0.0, T, 200001)
+    s = np.array([oracle_mod.ramp_s(knots, T, t) for t in tt[::100]])
+    S = np.trapezoid(np.interp(tt, tt[::100], s), tt)     # s is piecewise linear: exact
+    exact = sla.expm(-1j * H0 * T) @ psi0 * np.exp(-1j * S)
+    errs = []
+    for nsteps in (40, 80):
+        dt = T / nsteps
+        y = psi0
+        for q in range(nsteps):
+            y = oracle_mod.rk4_step(g, V0, y, 0.0, q * dt, dt, V1, knots, T)
+        errs.append(relerr(y, exact))
+    assert errs[0] / errs[1] > 12.0, errs
+
+
+def test_rk4_constant_knots_equal_static_blend(oracle_mod):
+    box = inputs.Box(5, 6, 5, 0.3, 0.3, 0.3)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 9), 0.3)
+    rng = np.random.default_rng(10)
+    V0, V1 = rng.uniform(0, 3, g.n), rng.uniform(0, 3, g.n)
+    psi = cvec(g.n, 11)
+    s = 0.37
+    a = oracle_mod.rk4_step(g, V0, psi, 2.0, 0.01, 0.003, V1, np.full(16, s), 1.0)
+    b = oracle_mod.rk4_step(g, (1 - s) * V0 + s * V1, psi, 2.0, 0.01, 0.003)
+    assert relerr(a, b) < 1e-15
+
+
+def test_rk4_norm_loss_matches_stability_polynomial(oracle_mod):
+    """For an eigenvector of H with eigenvalue E, one step multiplies it by
+    P4(-i E dt); the norm loss is 1 - |P4(i y)|^2 = y^6/72 - y^8/576, y = E dt."""
+    n, h = 20, 0.3
+    box = inputs.cubic_box(n, h)
+    g = oracle_mod.Grid(np.ones(box.shape, bool), h)
+    V = g.compact(inputs.dense_potential(box, inputs.Harmonic()))
+    lam, v = ho_1d(n, h)
+    psi = np.einsum("k,j,i->kji", v, v, v).astype(np.complex128).ravel()
+    dt = 0.35
+    y = 3 * lam * dt
+    out = oracle_mod.rk4_step(g, V, psi, 0.0, 0.0, dt)
+    loss = 1 - np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi) ** 2)
+    assert abs(loss - (y ** 6 / 72 - y ** 8 / 576)) < 1e-13
+
+
+def test_rk4_interacting_conserves_norm_and_energy(oracle_mod):
+    """g > 0: the exact flow of Eq. (2) conserves N and E; RK4 drift shrinks
+    at high order with dt (consistency of the RHS with the energy functional)."""
+    n, h, g_ = 20, 0.4, 50.0
+    box = inputs.cubic_box(n, h)
+    g = oracle_mod.Grid(np.ones(box.shape, bool), h)
+    V = g.compact(inputs.dense_potential(box, inputs.Harmonic(1.0, 1.3, 0.8)))
+    psi0 = g.compact(inputs.gaussian_with_noise(box, seed=3, noise=0.05))
+    o0 = oracle_mod.observables(g, V, g_, psi0)
+    drifts = []
+    for dt in (0.004, 0.002):
+        y = psi0
+        for q in range(int(0.2 / dt)):
+            y = oracle_mod.rk4_step(g, V, y, g_, q * dt, dt)
+        o = oracle_mod.observables(g, V, g_, y)
+        drifts.append((abs(o["norm"] - o0["norm"]), abs(o["energy"] - o0["energy"]) / abs(o0["energy"])))
+    assert drifts[0][0] < 1e-5 and drifts[0][1] < 1e-5
+    assert drifts[0][1] / drifts[1][1] > 10.0
+
+
+# ----------------------------------------------------------------- App. A tables
+def derive_memopt(a, b):
+    """Eq. (A4)-(A7): express k_j through the stage states by inverting M, then
+    collect the coefficients of y^(j) in y^(i+1) and in y1 (dt = 1)."""
+    n = len(b)
+    M = [[Fraction(0)] * n for _ in range(n)]
+    for i in range(n):
+        M[i][0] = Fraction(1)
+        for j in range(i):
+            M[i][j + 1] = a[i][j]
+    # exact inverse of the lower-triangular M
+    Minv = [[Fraction(0)] * n for _ in range(n)]
+    for col in range(n):
+        e = [Fraction(int(r == col)) for r in range(n)]
+        x = [Fraction(0)] * n
+        for r in range(n):
+            x[r] = (e[r] - sum(M[r][q] * x[q] for q in range(r))) / M[r][r]
+        for r in range(n):
+            Minv[r][col] = x[r]
+    a_star = []
+    for i in range(1, n):                     # row for y^(i+1), i = 1..n-1
+        row = [Fraction(int(m == 0)) for m in range(i)]
+        for j in range(1, i):                 # k_j, j < i, through Minv row j (K_{j+1})
+            for m in range(i):
+                row[m] += a[i][j - 1] * Minv[j][m]
+        a_star.append(row)
+    b_star = [Fraction(int(m == 0)) for m in range(n)]
+    for j in range(1, n):
+        for m in range(n):
+            b_star[m] += b[j - 1] * Minv[j][m]
+    return a_star, b_star
+
+
+F = Fraction
+TABLEAUS = {
+    "RKHE3": ([[], [F(1, 3)], [F(0), F(2, 3)]], [F(1, 4), F(0), F(3, 4)]),
+    "RK4": ([[], [F(1, 2)], [F(0), F(1, 2)], [F(0), F(0), F(1)]], [F(1, 6), F(1, 3), F(1, 3), F(1, 6)]),
+    "RKCK": ([[], [F(1, 5)], [F(3, 40), F(9, 40)], [F(3, 10), F(-9, 10), F(6, 5)],
+              [F(-11, 54), F(5, 2), F(-70, 27), F(35, 27)],
+              [F(1631, 55296), F(175, 512), F(575, 13824), F(44275, 110592), F(253, 4096)]],
+             [F(37, 378), F(0), F(250, 621), F(125, 594), F(0), F(512, 1771)]),
+}
+
+
+@pytest.mark.parametrize("method", ["RKHE3", "RK4", "RKCK"])
+def test_memory_optimized_tables_match_appendix_A(method):
+    gold = json.load(open(os.path.join(GOLDEN, "memopt_rk_appA.json")))[method]
+    a, b = TABLEAUS[method]
+    a_star, b_star = derive_memopt(a, b)
+    want_a = [[Fraction(v) for v in row] for row in gold["a_star"]]
+    want_b = [Fraction(v) for v in gold["b_star"]]
+    for i, row in enumerate(want_a):
+        assert a_star[i] == row[: i + 1] and all(v == 0 for v in row[i + 1:]), (i, a_star[i], row)
+    assert b_star == want_b
+
+
+def test_memory_optimized_rk4_stage_algebra_equals_butcher_step(oracle_mod):
+    """The stage recurrences used by the CUDA kernels (App. A, RK4 a*, b*)
+    reproduce the oracle's Butcher-form step to round-off."""
+    box = inputs.Box(6, 5, 7, 0.3, 0.3, 0.3)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 12), 0.3)
+    V = np.random.default_rng(13).uniform(0, 3, g.n)
+    y0 = cvec(g.n, 14) * 0.3
+    dt, g_ = 0.003, 4.0
+    f = lambda y: oracle_mod.rhs_real(g, V, g_, y)
+    y2 = y0 + dt / 2 * f(y0)
+    y3 = y0 + dt / 2 * f(y2)
+    y4 = y0 + dt * f(y3)
+    y1 = -y0 / 3 + y2 / 3 + 2 * y3 / 3 + y4 / 3 + dt / 6 * f(y4)
+    assert relerr(y1, oracle_mod.rk4_step(g, V, y0, g_, 0.0, dt)) < 1e-14
+
+
+# ----------------------------------------------------------------- adjoint
+def ramp_problem(oracle_mod, seed=0):
+    box = inputs.Box(6, 6, 6, 0.4, 0.4, 0.4)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.85, 30 + seed), 0.4)
+    x, y, z = box.coords_of(g.ijk())
+    V0 = 0.5 * (x * x + y * y + z * z)
+    V1 = 2.0 * (np.sqrt(x * x + y * y + z * z) - 0.8) ** 2
+    rng = np.random.default_rng(40 + seed)
+    psi0 = (np.exp(-(x * x + y * y + z * z)) * (1 + 0.1 * rng.standard_normal(g.n))).astype(np.complex128)
+    psi0 /= math.sqrt(np.sum(np.abs(psi0) ** 2) * g.dV)
+    tgt = (np.exp(-2 * (np.sqrt(x * x + y * y + z * z) - 0.8) ** 2)).astype(np.complex128)
+    tgt /= math.sqrt(np.sum(np.abs(tgt) ** 2) * g.dV)
+    knots = inputs.monotone_knots(16, seed=3)
+    return g, V0, V1, psi0, tgt, knots
+
+
+def test_adjoint_gradient_matches_central_differences(oracle_mod):
+    g, V0, V1, psi0, tgt, knots = ramp_problem(oracle_mod)
+    T, dt, nsteps, g_ = 0.3, 0.01, 30, 20.0
+    loss, grad, _ = oracle_mod.ramp_loss_and_grad(g, V0, V1, knots, T, g_, dt, nsteps, psi0, tgt)
+    eps = 1e-4
+    fd = np.zeros_like(grad)
+    for q in range(len(knots)):
+        kp, km = knots.copy(), knots.copy()
+        kp[q] += eps
+        km[q] -= eps
+        lp = oracle_mod.ramp_loss_and_grad(g, V0, V1, kp, T, g_, dt, nsteps, psi0, tgt)[0]
+        lm = oracle_mod.ramp_loss_and_grad(g, V0, V1, km, T, g_, dt, nsteps, psi0, tgt)[0]
+        fd[q] = (lp - lm) / (2 * eps)
+    assert np.max(np.abs(grad - fd)) / np.max(np.abs(fd)) < 1e-6
+
+
+def test_adjoint_step_transpose_identity(oracle_mod):
+    """<lam, J v> = <J^T lam, v> (real inner product of real pairs) for one step,
+    J v from a central directional difference of the forward step."""
+    g, V0, V1, psi0, tgt, knots = ramp_problem(oracle_mod, seed=1)
+    T, dt, g_, t = 0.3, 0.01, 20.0, 0.05
+    v = cvec(g.n, 50)
+    lam = cvec(g.n, 51)
+    eps = 1e-6
+    fp = oracle_mod.rk4_step(g, V0, psi0 + eps * v, g_, t, dt, V1, knots, T)
+    fm = oracle_mod.rk4_step(g, V0, psi0 - eps * v, g_, t, dt, V1, knots, T)
+    Jv = (fp - fm) / (2 * eps)
+    JTlam, _ = oracle_mod.rk4_adjoint_step(g, V0, V1, knots, T, g_, t, dt, psi0, lam)
+    lhs = np.sum(np.real(np.conj(lam) * Jv))
+    rhs = np.sum(np.real(np.conj(JTlam) * v))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-8
