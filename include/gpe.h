@@ -1,0 +1,280 @@
+/*
+ * gpe.h -- C ABI of libgpeshell: the finite-difference Gross-Pitaevskii (GPE)
+ * step on a selectively sampled ("semi-structured") Cartesian grid, on one
+ * NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Beregi, Gerent, Lundblad, "Efficient simulation of Bose-Einstein
+ * condensates in nontrivial topologies".  Units hbar = m = 1.  The problem is
+ * the paper's own statement of it (Sec. II): a potential V on a Cartesian grid
+ * and a cutoff select a region of interest; psi is stepped in imaginary time
+ * (Eqs. (6)-(7), ground state with renormalisation to N, Eq. (3)) or in real
+ * time (Eq. (8), explicit Runge-Kutta); norm, energy and chemical potential are
+ * reported.
+ *
+ * Conventions (every call):
+ *  - Every function returns GPE_OK (0) or a negative GPE_ERR_* code; on error
+ *    gpe_last_error() returns a one-line description (thread-local).  No C++
+ *    exception crosses this ABI.
+ *  - Handles (gpe_grid, gpe_state, gpe_batch, gpe_tape) are opaque, created and
+ *    freed by the library, and bound to the CUDA device that was current when
+ *    they were created.  Calls on a handle must be made with that device
+ *    current.
+ *  - Host pointers are read or written before the call returns and are never
+ *    retained.  Device pointers are borrowed for the duration of the call (the
+ *    copy is ordered on `stream`; the caller keeps the memory alive until the
+ *    stream has passed it).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls documented as asynchronous only enqueue work on it; calls
+ *    that return results on the host synchronise that stream.
+ *  - Complex arrays are interleaved (re, im) pairs: complex64 = two float32,
+ *    complex128 = two float64.
+ *  - Dense box arrays are laid out x fastest: cell (i, j, k) at linear index
+ *    i + nx*(j + ny*k); cell centres at (x0 + i*hx, y0 + j*hy, z0 + k*hz).
+ *  - The compact ("stored") layout is the library's device layout: bricks of
+ *    bx*by*bz cells, brick b at offset b*bx*by*bz, cells inside a brick x
+ *    fastest.  Stored cells that are not active hold zero.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    GPE_OK = 0,
+    GPE_ERR_ARG = -1,           /* invalid argument (checked before any GPU work) */
+    GPE_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    GPE_ERR_OOM = -3,           /* device allocation failed */
+    GPE_ERR_NONFINITE = -4,     /* a reduction saw NaN or Inf in psi */
+    GPE_ERR_UNSTABLE = -5,      /* dt beyond the integrator's stability bound */
+    GPE_ERR_NOT_CONVERGED = -6, /* ground-state iteration hit max_steps */
+    GPE_ERR_STATE = -7          /* handle in the wrong state for this call */
+};
+
+typedef void *gpe_stream; /* cudaStream_t */
+
+typedef struct gpe_grid gpe_grid;
+typedef struct gpe_state gpe_state;
+typedef struct gpe_batch gpe_batch;
+typedef struct gpe_tape gpe_tape;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int gpe_version(void);
+
+/* Copy the calling thread's last error message into buf (NUL-terminated,
+ * truncated to n bytes).  Returns the length of the full message. */
+int gpe_last_error(char *buf, size_t n);
+
+/* ------------------------------------------------------------------ grids */
+/* Cartesian bounding box.  (x0, y0, z0) is the centre of cell (0, 0, 0). */
+typedef struct gpe_box {
+    int64_t nx, ny, nz;
+    double hx, hy, hz;
+    double x0, y0, z0;
+} gpe_box;
+
+enum { GPE_MASK_CELL = 0,   /* active = cells with V < V_cut (Sec. II A) */
+       GPE_MASK_BRICK = 1 }; /* active = every in-box cell of a brick holding
+                                at least one cell with V < V_cut (Sec. II B) */
+enum { GPE_ORDER_MORTON = 0, GPE_ORDER_ZMAJOR = 1 };
+
+/* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
+ * all three are 0), 8x8x4, 8x4x4, 4x4x4. */
+typedef struct gpe_grid_opts {
+    int32_t bx, by, bz;
+    int32_t mask_mode; /* GPE_MASK_* */
+    int32_t order;     /* GPE_ORDER_* : order of the brick list in memory */
+    int32_t reserved[3];
+} gpe_grid_opts;
+
+enum { GPE_F64 = 1, GPE_F32 = 2 };   /* element type of a real input array */
+
+/* Analytic potentials evaluated on the device (needed for boxes whose dense
+ * potential does not fit in memory):
+ *   GPE_POT_HARMONIC        V = 1/2 (p0^2 x^2 + p1^2 y^2 + p2^2 z^2)
+ *   GPE_POT_ELLIPSOID_SHELL V = 1/2 p0^2 (rho - 1)^2,
+ *                           rho = sqrt(x^2/p1^2 + y^2/p2^2 + z^2/p3^2)
+ * Unused parameters must be zero. */
+enum { GPE_POT_HARMONIC = 1, GPE_POT_ELLIPSOID_SHELL = 2 };
+typedef struct gpe_potential {
+    int32_t kind;
+    int32_t reserved;
+    double p[8];
+} gpe_potential;
+
+/* Build a grid from a dense potential V (nx*ny*nz values of type V_dtype, on
+ * the host or the device) and a cutoff: the region of interest is the set of
+ * cells with V < V_cut (Sec. II A, region of interest from the Thomas-Fermi
+ * estimate of Eq. (5); the caller picks V_cut, e.g. 5 mu).  The active cells
+ * are compacted into bricks (Sec. II B), ordered by opts->order, with a
+ * brick-neighbour table; absent neighbours read as psi = 0 (rows and columns
+ * deleted from the Laplacian, Sec. II A).  Potential slot 0 holds V.
+ * opts may be NULL (8x8x8, cell mask, Morton order).  Synchronous. */
+int gpe_grid_create_dense(const gpe_box *box, const void *V, int V_dtype,
+                          int V_on_device, double V_cut,
+                          const gpe_grid_opts *opts, gpe_grid **out,
+                          gpe_stream stream);
+
+/* Same, with V evaluated on the device from an analytic description. */
+int gpe_grid_create_analytic(const gpe_box *box, const gpe_potential *pot,
+                             double V_cut, const gpe_grid_opts *opts,
+                             gpe_grid **out, gpe_stream stream);
+
+/* Grid for a potential ramp V(t) = (1 - s) V0 + s V1 (Sec. V: linear
+ * interpolation between precomputed potentials).  With the cutoff blended the
+ * same way, the union over s in [0, 1] of {V(s) < cut(s)} is exactly
+ * {V0 < cut0} U {V1 < cut1}; that union is the region of interest.  Slot 0
+ * holds V0 and slot 1 holds V1.  Synchronous. */
+int gpe_grid_create_blend(const gpe_box *box, const gpe_potential *pot0,
+                          double cut0, const gpe_potential *pot1, double cut1,
+                          const gpe_grid_opts *opts, gpe_grid **out,
+                          gpe_stream stream);
+
+/* Replace potential slot 0 or 1 with a dense potential (same layout as
+ * gpe_grid_create_dense); the region of interest is unchanged.  Synchronous. */
+int gpe_grid_set_potential(gpe_grid *grid, int slot, const void *V,
+                           int V_dtype, int V_on_device, gpe_stream stream);
+
+typedef struct gpe_grid_info {
+    int64_t n_active;  /* cells in the region of interest */
+    int64_t n_bricks;
+    int64_t n_stored;  /* n_bricks * bx*by*bz */
+    int32_t bx, by, bz, mask_mode;
+    int32_t order, n_slots; /* number of potential slots filled (1 or 2) */
+    double v_max;      /* max of |V| over active cells, all slots */
+    gpe_box box;
+} gpe_grid_info;
+
+int gpe_grid_get_info(const gpe_grid *grid, gpe_grid_info *out);
+
+/* Host copies of the layout: brick origins in cells (3 int32 per brick,
+ * i0 j0 k0), the neighbour table (6 int32 per brick: -x +x -y +y -z +z, -1 =
+ * absent; may be NULL), the active-cell bit mask (n_stored/32 words, bit l of
+ * word w = stored cell 32w + l), and potential slot `slot` (n_stored doubles).
+ * Synchronous. */
+int gpe_grid_bricks(const gpe_grid *grid, int32_t *origins, int32_t *nbr);
+int gpe_grid_mask(const gpe_grid *grid, uint32_t *bits);
+int gpe_grid_potential(const gpe_grid *grid, int slot, double *V);
+
+int gpe_grid_destroy(gpe_grid *grid);
+
+/* Thomas-Fermi chemical potential (Sec. II A, Eq. (5)): the mu at which
+ * sum over the box of max((mu - V)/g, 0) dV equals N, found by bisection on
+ * the device.  Synchronous. */
+int gpe_tf_mu_dense(const gpe_box *box, const void *V, int V_dtype,
+                    int V_on_device, double g, double N, double *mu,
+                    gpe_stream stream);
+int gpe_tf_mu_analytic(const gpe_box *box, const gpe_potential *pot,
+                       double g, double N, double *mu, gpe_stream stream);
+
+/* ------------------------------------------------------------------ states */
+enum { GPE_C128 = 1, GPE_C64 = 2 };
+enum { GPE_LAYOUT_DENSE = 0, GPE_LAYOUT_COMPACT = 1 };
+
+/* A wavefunction on a grid, complex128 or complex64 (bulk precision).  The
+ * state keeps a reference to the grid: destroy states before their grid. */
+int gpe_state_create(gpe_grid *grid, int dtype, gpe_state **out);
+
+/* Load psi from a dense box array (inactive cells are ignored) or from the
+ * compact layout (inactive slots are forced to zero).  Asynchronous for device
+ * input; host input is staged through the library and the call returns once
+ * the host buffer has been read. */
+int gpe_state_load(gpe_state *st, const void *psi, int layout, int on_device,
+                   gpe_stream stream);
+
+/* Store psi to a dense box array (cells outside the region are zero) or to the
+ * compact layout.  Asynchronous for device output; synchronous for host. */
+int gpe_state_store(const gpe_state *st, void *psi, int layout, int on_device,
+                    gpe_stream stream);
+
+/* dst <- src (same grid and dtype).  Asynchronous. */
+int gpe_state_copy(gpe_state *dst, const gpe_state *src, gpe_stream stream);
+
+/* Device pointer of the compact psi array (borrowed; valid until destroy). */
+int gpe_state_device_ptr(gpe_state *st, void **dptr);
+
+int gpe_state_destroy(gpe_state *st);
+
+/* ------------------------------------------------------------------ steps */
+/* Imaginary time (Sec. II A, Eqs. (6)-(7)).  Each step, in the paper's order:
+ *  psi <- psi exp(-V dt/2) (1 - g|psi|^2 dt/2)    (diagonal half step)
+ *  psi <- psi - (dt/2) T psi, twice               (kinetic: two Euler steps)
+ *  psi <- psi exp(-V dt/2) (1 - g|psi|^2 dt/2)    (diagonal half step)
+ *  psi <- psi sqrt(N / sum |psi|^2 dV)            (renormalise, Eq. (3))
+ * with T = -1/2 Laplacian (7 point, Eq. (B1)) and V from slot 0.  The
+ * renormalisation factor is computed on the device in FP64 and applied when
+ * the next step loads psi (Sec. II B); the state is fully normalised when the
+ * call's work completes.  Asynchronous.  GPE_ERR_UNSTABLE if
+ * dt * sum_e 2/h_e^2 > 4 (the Euler substep would amplify the top mode). */
+typedef struct gpe_imag_params {
+    double g, dt, N;
+} gpe_imag_params;
+
+int gpe_step_imag(gpe_state *st, const gpe_imag_params *p, int64_t nsteps,
+                  gpe_stream stream);
+
+/* Real time (Sec. II A, Eq. (8)) with the classic RK4 method in the
+ * memory-optimised stage form of App. A:
+ *   y2 = y0 + dt/2 f(t, y0);  y3 = y0 + dt/2 f(t + dt/2, y2);
+ *   y4 = y0 + dt f(t + dt/2, y3);
+ *   y1 = -y0/3 + y2/3 + 2 y3/3 + y4/3 + dt/6 f(t + dt, y4)
+ * f(t, y) = -i (T + V(t) + g|y|^2) y.  V(t) = V0 (GPE_V_STATIC) or
+ * (1 - s(t)) V0 + s(t) V1 (GPE_V_BLEND) with s piecewise linear through
+ * n_knots (2..16) values at uniform times on [0, T_ramp], constant outside.
+ * t0 is the time at the start of the first step.  Asynchronous.
+ * GPE_ERR_UNSTABLE if dt (sum_e 2/h_e^2 + v_max) > 2 sqrt(2) (RK4's
+ * imaginary-axis stability limit for the linear part). */
+enum { GPE_RK4 = 0 };
+enum { GPE_V_STATIC = 0, GPE_V_BLEND = 1 };
+#define GPE_MAX_KNOTS 16
+typedef struct gpe_real_params {
+    double g, dt;
+    int32_t integrator; /* GPE_RK4 */
+    int32_t potential;  /* GPE_V_* */
+    int32_t n_knots, reserved;
+    double T_ramp;
+    double knots[GPE_MAX_KNOTS];
+} gpe_real_params;
+
+int gpe_step_real(gpe_state *st, const gpe_real_params *p, int64_t nsteps,
+                  double t0, gpe_stream stream);
+
+/* ------------------------------------------------------------------ observables */
+/* FP64 reductions over the active cells (products in the state's precision):
+ *   norm   = sum |psi|^2 dV                           (Eq. (3))
+ *   e_kin  = sum Re(conj(psi) T psi) dV
+ *   e_pot  = sum V |psi|^2 dV,  V = (1 - s_blend) V0 + s_blend V1
+ *   e_int  = sum (g/2) |psi|^4 dV
+ *   energy = e_kin + e_pot + e_int
+ *   mu     = (e_kin + e_pot + 2 e_int) / norm   (Eq. (1) projected on psi)
+ *   nonfinite = number of active cells holding NaN or Inf.
+ * Synchronous; returns GPE_ERR_NONFINITE (with *out filled) when
+ * nonfinite > 0. */
+typedef struct gpe_obs {
+    double norm, energy, mu, nonfinite, e_kin, e_pot, e_int;
+} gpe_obs;
+
+int gpe_observables(const gpe_state *st, double g, double s_blend,
+                    gpe_obs *out, gpe_stream stream);
+
+/* out = <a|b> = sum conj(a) b dV as (re, im).  Synchronous. */
+int gpe_overlap(const gpe_state *a, const gpe_state *b, double out[2],
+                gpe_stream stream);
+
+/* Imaginary-time ground state (Sec. III: iterate to a tolerance): gpe_step_imag
+ * in blocks of check_every steps until |mu_n - mu_{n-1}| < tol_dmu between two
+ * checks.  *steps_done and *obs (may be NULL) report the last check.
+ * GPE_ERR_NOT_CONVERGED after max_steps.  Synchronous. */
+int gpe_ground_state(gpe_state *st, const gpe_imag_params *p, double tol_dmu,
+                     int64_t check_every, int64_t max_steps,
+                     int64_t *steps_done, gpe_obs *obs, gpe_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPE_H */

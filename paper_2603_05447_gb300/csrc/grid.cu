@@ -1,0 +1,803 @@
+// grid.cu -- region-of-interest selection and brick compaction (Sec. II A and
+// Sec. II B of the paper), built on the device.
+//
+// Steps: (1) brick occupancy over the brick grid covering the box (a brick is
+// kept if any of its in-box cells has V < V_cut); (2) enumeration of the brick
+// grid in Morton or z-major key order with an order-preserving compaction (two
+// passes: per-block counts, then emission at scanned offsets); (3) a dense
+// brick-id volume and the 6-entry face-neighbour table; (4) per-cell potential
+// values and the active-cell bit mask.  The paper's GPU variant keeps a
+// 488-entry halo index list per 8^3 block (Sec. II B); here six neighbour ids
+// per brick are enough because the halo is gathered from neighbour bricks at
+// fixed offsets inside the step kernels.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "gpe_internal.cuh"
+
+namespace gpe {
+
+struct PotDesc {
+    int kind;
+    double p[8];
+};
+
+// V source for the builder: dense array, one analytic potential, or two
+// (ramp endpoints) whose union mask is taken.
+struct VSource {
+    int mode;  // 0 dense, 1 analytic, 2 blend
+    const void *dense;
+    int dtype;
+    PotDesc p0, p1;
+    double cut0, cut1;
+};
+
+__device__ __forceinline__ double eval_pot(const PotDesc &P, double x, double y, double z)
+{
+    if (P.kind == GPE_POT_HARMONIC)
+        return 0.5 * (P.p[0] * P.p[0] * x * x + P.p[1] * P.p[1] * y * y + P.p[2] * P.p[2] * z * z);
+    if (P.kind == GPE_POT_ELLIPSOID_SHELL) {
+        double rho = sqrt(x * x / (P.p[1] * P.p[1]) + y * y / (P.p[2] * P.p[2]) +
+                          z * z / (P.p[3] * P.p[3]));
+        double d = rho - 1.0;
+        return 0.5 * P.p[0] * P.p[0] * d * d;
+    }
+    return 0.0;
+}
+
+struct BoxD {
+    int64_t nx, ny, nz;
+    double hx, hy, hz, x0, y0, z0;
+};
+
+__device__ __forceinline__ void cell_values(const VSource &src, const BoxD &bx, int64_t i,
+                                            int64_t j, int64_t k, double &v0, double &v1,
+                                            bool &sel)
+{
+    if (src.mode == 0) {
+        int64_t lin = i + bx.nx * (j + bx.ny * k);
+        v0 = src.dtype == GPE_F64 ? ((const double *)src.dense)[lin]
+                                  : (double)((const float *)src.dense)[lin];
+        v1 = 0.0;
+        sel = v0 < src.cut0;
+        return;
+    }
+    double x = bx.x0 + i * bx.hx, y = bx.y0 + j * bx.hy, z = bx.z0 + k * bx.hz;
+    v0 = eval_pot(src.p0, x, y, z);
+    if (src.mode == 2) {
+        v1 = eval_pot(src.p1, x, y, z);
+        sel = (v0 < src.cut0) || (v1 < src.cut1);
+    } else {
+        v1 = 0.0;
+        sel = v0 < src.cut0;
+    }
+}
+
+// (1) occupancy of every brick-grid position (lexicographic q)
+__global__ void k_occupancy(VSource src, BoxD box, int BX, int BY, int BZ, int64_t nbx,
+                            int64_t nby, int64_t nbz, uint8_t *occ)
+{
+    const int64_t q = blockIdx.x + (int64_t)gridDim.x * blockIdx.y;
+    if (q >= nbx * nby * nbz) return;
+    const int64_t qx = q % nbx, qy = (q / nbx) % nby, qz = q / (nbx * nby);
+    const int BC = BX * BY * BZ;
+    int sel_any = 0;
+    for (int l = threadIdx.x; l < BC; l += blockDim.x) {
+        int64_t i = qx * BX + l % BX, j = qy * BY + (l / BX) % BY, k = qz * BZ + l / (BX * BY);
+        if (i < box.nx && j < box.ny && k < box.nz) {
+            double v0, v1;
+            bool sel;
+            cell_values(src, box, i, j, k, v0, v1, sel);
+            sel_any |= sel;
+        }
+    }
+    sel_any = __syncthreads_or(sel_any);
+    if (threadIdx.x == 0) occ[q] = (uint8_t)(sel_any != 0);
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t m)
+{
+    // keep every third bit of m (bit 3n -> bit n)
+    uint64_t x = m & 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+struct Enum {
+    int order;  // GPE_ORDER_*
+    int64_t nbx, nby, nbz;
+    uint64_t nkeys;
+};
+
+__device__ __forceinline__ bool key_brick(const Enum &E, const uint8_t *occ, uint64_t key,
+                                          int64_t &bx, int64_t &by, int64_t &bz)
+{
+    if (E.order == GPE_ORDER_MORTON) {
+        bx = compact3(key);
+        by = compact3(key >> 1);
+        bz = compact3(key >> 2);
+        if (bx >= E.nbx || by >= E.nby || bz >= E.nbz) return false;
+    } else {
+        bx = key % E.nbx;
+        by = (key / E.nbx) % E.nby;
+        bz = key / (E.nbx * E.nby);
+    }
+    return occ[bx + E.nbx * (by + E.nby * bz)] != 0;
+}
+
+constexpr int ENUM_THREADS = 256, ENUM_PER_THREAD = 4;
+constexpr int ENUM_PER_BLOCK = ENUM_THREADS * ENUM_PER_THREAD;
+
+// (2a) number of kept bricks per enumeration block
+__global__ void k_enum_count(Enum E, const uint8_t *occ, int64_t *bsum)
+{
+    const uint64_t base = (uint64_t)blockIdx.x * ENUM_PER_BLOCK + threadIdx.x * ENUM_PER_THREAD;
+    int c = 0;
+    for (int r = 0; r < ENUM_PER_THREAD; ++r) {
+        uint64_t key = base + r;
+        int64_t bx, by, bz;
+        if (key < E.nkeys && key_brick(E, occ, key, bx, by, bz)) ++c;
+    }
+    __shared__ int warp_tot[ENUM_THREADS / 32];
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < ENUM_THREADS / 32; ++w) s += warp_tot[w];
+        bsum[blockIdx.x] = s;
+    }
+}
+
+// (2b) emit kept bricks in key order at the scanned block offsets
+__global__ void k_enum_emit(Enum E, const uint8_t *occ, const int64_t *boff, int32_t *coords)
+{
+    __shared__ int warp_tot[ENUM_THREADS / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * ENUM_PER_BLOCK + threadIdx.x * ENUM_PER_THREAD;
+    int c = 0;
+    for (int r = 0; r < ENUM_PER_THREAD; ++r) {
+        uint64_t key = base + r;
+        int64_t bx, by, bz;
+        if (key < E.nkeys && key_brick(E, occ, key, bx, by, bz)) ++c;
+    }
+    // exclusive scan of c over threads (in thread order = key order)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += warp_tot[w];
+    int64_t pos = boff[blockIdx.x] + wpre + incl - c;
+    for (int r = 0; r < ENUM_PER_THREAD; ++r) {
+        uint64_t key = base + r;
+        int64_t bx, by, bz;
+        if (key < E.nkeys && key_brick(E, occ, key, bx, by, bz)) {
+            coords[3 * pos + 0] = (int32_t)bx;
+            coords[3 * pos + 1] = (int32_t)by;
+            coords[3 * pos + 2] = (int32_t)bz;
+            ++pos;
+        }
+    }
+}
+
+// (3) brick-id volume, origins, neighbour table
+__global__ void k_bricks(int64_t nb, const int32_t *coords, int BX, int BY, int BZ,
+                         int64_t nbx, int64_t nby, int32_t *bvol, int32_t *org)
+{
+    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nb) return;
+    int64_t bx = coords[3 * id], by = coords[3 * id + 1], bz = coords[3 * id + 2];
+    bvol[bx + nbx * (by + nby * bz)] = (int32_t)id;
+    org[3 * id + 0] = (int32_t)(bx * BX);
+    org[3 * id + 1] = (int32_t)(by * BY);
+    org[3 * id + 2] = (int32_t)(bz * BZ);
+}
+
+__global__ void k_neighbors(int64_t nb, const int32_t *coords, int64_t nbx, int64_t nby,
+                            int64_t nbz, const int32_t *bvol, int32_t *nbr)
+{
+    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nb) return;
+    const int64_t c[3] = {coords[3 * id], coords[3 * id + 1], coords[3 * id + 2]};
+    const int64_t n[3] = {nbx, nby, nbz};
+    for (int d = 0; d < 6; ++d) {
+        int64_t q[3] = {c[0], c[1], c[2]};
+        q[d >> 1] += (d & 1) ? 1 : -1;
+        int32_t r = -1;
+        if (q[d >> 1] >= 0 && q[d >> 1] < n[d >> 1]) r = bvol[q[0] + nbx * (q[1] + nby * q[2])];
+        nbr[6 * id + d] = r;
+    }
+}
+
+// (4) per-cell potential values and active bits; one block per brick
+__global__ void k_cells(VSource src, BoxD box, int BX, int BY, int BZ, int mask_mode,
+                        const int32_t *org, double *V0, double *V1, uint32_t *mask,
+                        unsigned long long *n_active, unsigned long long *vmax_bits)
+{
+    const int64_t id = blockIdx.x;
+    const int BC = BX * BY * BZ;
+    unsigned long long cnt = 0;
+    double vm = 0.0;
+    for (int l = threadIdx.x; l < BC; l += blockDim.x) {  // BC % 32 == 0, blockDim % 32 == 0
+        int64_t i = org[3 * id] + l % BX, j = org[3 * id + 1] + (l / BX) % BY,
+                k = org[3 * id + 2] + l / (BX * BY);
+        bool inbox = i < box.nx && j < box.ny && k < box.nz;
+        double v0 = 0.0, v1 = 0.0;
+        bool sel = false;
+        if (inbox) cell_values(src, box, i, j, k, v0, v1, sel);
+        bool act = inbox && (mask_mode == GPE_MASK_BRICK ? true : sel);
+        const int64_t slot = id * BC + l;
+        V0[slot] = v0;
+        if (V1) V1[slot] = v1;
+        unsigned bits = __ballot_sync(0xffffffffu, act);
+        if ((threadIdx.x & 31) == 0) mask[slot >> 5] = bits;
+        if (act) {
+            ++cnt;
+            vm = fmax(vm, fabs(v0));
+            if (V1) vm = fmax(vm, fabs(v1));
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+        vm = fmax(vm, __shfl_down_sync(0xffffffffu, vm, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(n_active, cnt);
+        atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(vm));
+    }
+}
+
+// replace a potential slot from a dense array (region unchanged)
+__global__ void k_set_potential(const void *dense, int dtype, BoxD box, int BX, int BY, int BZ,
+                                const int32_t *org, double *V)
+{
+    const int64_t id = blockIdx.x;
+    const int BC = BX * BY * BZ;
+    for (int l = threadIdx.x; l < BC; l += blockDim.x) {
+        int64_t i = org[3 * id] + l % BX, j = org[3 * id + 1] + (l / BX) % BY,
+                k = org[3 * id + 2] + l / (BX * BY);
+        double v = 0.0;
+        if (i < box.nx && j < box.ny && k < box.nz) {
+            int64_t lin = i + box.nx * (j + box.ny * k);
+            v = dtype == GPE_F64 ? ((const double *)dense)[lin] : (double)((const float *)dense)[lin];
+        }
+        V[id * BC + l] = v;
+    }
+}
+
+__global__ void k_vmax(int64_t ns, const uint32_t *mask, const double *V0, const double *V1,
+                       unsigned long long *vmax_bits)
+{
+    double vm = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if ((mask[s >> 5] >> (s & 31)) & 1u) {
+            vm = fmax(vm, fabs(V0[s]));
+            if (V1) vm = fmax(vm, fabs(V1[s]));
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) vm = fmax(vm, __shfl_down_sync(0xffffffffu, vm, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(vm));
+}
+
+static BoxD boxd(const gpe_box &b)
+{
+    return BoxD{b.nx, b.ny, b.nz, b.hx, b.hy, b.hz, b.x0, b.y0, b.z0};
+}
+
+static int check_box(const gpe_box *box)
+{
+    if (!box) return fail(GPE_ERR_ARG, "box is NULL");
+    if (box->nx < 1 || box->ny < 1 || box->nz < 1)
+        return fail(GPE_ERR_ARG, "box dimensions must be >= 1 (got %lld x %lld x %lld)",
+                    (long long)box->nx, (long long)box->ny, (long long)box->nz);
+    if (!(box->hx > 0) || !(box->hy > 0) || !(box->hz > 0))
+        return fail(GPE_ERR_ARG, "grid spacings must be > 0");
+    if (box->nx > (1 << 24) || box->ny > (1 << 24) || box->nz > (1 << 24))
+        return fail(GPE_ERR_ARG, "box dimension above 2^24");
+    return GPE_OK;
+}
+
+static int check_pot(const gpe_potential *p)
+{
+    if (!p) return fail(GPE_ERR_ARG, "potential is NULL");
+    if (p->kind != GPE_POT_HARMONIC && p->kind != GPE_POT_ELLIPSOID_SHELL)
+        return fail(GPE_ERR_ARG, "unknown potential kind %d", p->kind);
+    if (p->kind == GPE_POT_ELLIPSOID_SHELL && (!(p->p[1] > 0) || !(p->p[2] > 0) || !(p->p[3] > 0)))
+        return fail(GPE_ERR_ARG, "ellipsoid semi-axes must be > 0");
+    return GPE_OK;
+}
+
+static PotDesc potdesc(const gpe_potential &p)
+{
+    PotDesc d;
+    d.kind = p.kind;
+    for (int i = 0; i < 8; ++i) d.p[i] = p.p[i];
+    return d;
+}
+
+static void grid_free(gpe_grid *g)
+{
+    if (!g) return;
+    dev_free(g->d_org);
+    dev_free(g->d_nbr);
+    dev_free(g->d_mask);
+    dev_free(g->d_bvol);
+    for (int s = 0; s < 2; ++s) {
+        dev_free(g->d_V[s]);
+        dev_free(g->d_Vf[s]);
+    }
+    delete g;
+}
+
+// Build the grid; `src.dense` (mode 0) is a device pointer here.
+static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opts *opts,
+                      gpe_grid **out, cudaStream_t st)
+{
+    gpe_grid_opts o{};
+    if (opts) o = *opts;
+    if (o.bx == 0 && o.by == 0 && o.bz == 0) o.bx = o.by = o.bz = 8;
+    const int shape = shape_id(o.bx, o.by, o.bz);
+    if (shape < 0)
+        return fail(GPE_ERR_ARG, "unsupported brick shape %dx%dx%d (use 8x8x8, 8x8x4, 8x4x4, 4x4x4)",
+                    o.bx, o.by, o.bz);
+    if (o.mask_mode != GPE_MASK_CELL && o.mask_mode != GPE_MASK_BRICK)
+        return fail(GPE_ERR_ARG, "unknown mask mode %d", o.mask_mode);
+    if (o.order != GPE_ORDER_MORTON && o.order != GPE_ORDER_ZMAJOR)
+        return fail(GPE_ERR_ARG, "unknown brick order %d", o.order);
+
+    gpe_grid *g = new gpe_grid();
+    GPE_TRY_CUDA(cudaGetDevice(&g->device));
+    g->nsm = sm_count(g->device);
+    g->box = *box;
+    g->bx = o.bx;
+    g->by = o.by;
+    g->bz = o.bz;
+    g->bc = o.bx * o.by * o.bz;
+    g->shape = shape;
+    g->mask_mode = o.mask_mode;
+    g->order = o.order;
+    g->nbx = (box->nx + o.bx - 1) / o.bx;
+    g->nby = (box->ny + o.by - 1) / o.by;
+    g->nbz = (box->nz + o.bz - 1) / o.bz;
+    const int64_t nq = g->nbx * g->nby * g->nbz;
+    const BoxD bd = boxd(*box);
+
+    uint8_t *occ = nullptr;
+    int64_t *bsum = nullptr;
+    int32_t *coords = nullptr;
+    unsigned long long *counters = nullptr;
+    int rc = GPE_OK;
+    auto cleanup = [&]() {
+        dev_free(occ);
+        dev_free(bsum);
+        dev_free(coords);
+        dev_free(counters);
+    };
+#define BUILD_TRY(x)                 \
+    do {                             \
+        rc = (x);                    \
+        if (rc != GPE_OK) {          \
+            cleanup();               \
+            grid_free(g);            \
+            return rc;               \
+        }                            \
+    } while (0)
+#define BUILD_CUDA(x)                                                        \
+    do {                                                                     \
+        cudaError_t e__ = (x);                                               \
+        if (e__ != cudaSuccess) {                                            \
+            rc = cuda_fail(e__, #x, __FILE__, __LINE__);                     \
+            cleanup();                                                       \
+            grid_free(g);                                                    \
+            return rc;                                                       \
+        }                                                                    \
+    } while (0)
+
+    BUILD_TRY(dev_alloc_t(&occ, nq));
+    {
+        const int64_t gx = std::min<int64_t>(nq, 65535);
+        dim3 grid((unsigned)gx, (unsigned)((nq + gx - 1) / gx));
+        k_occupancy<<<grid, 128, 0, st>>>(src, bd, o.bx, o.by, o.bz, g->nbx, g->nby, g->nbz, occ);
+        BUILD_CUDA(cudaGetLastError());
+    }
+    Enum E;
+    E.order = o.order;
+    E.nbx = g->nbx;
+    E.nby = g->nby;
+    E.nbz = g->nbz;
+    if (o.order == GPE_ORDER_MORTON) {
+        int64_t m = std::max(g->nbx, std::max(g->nby, g->nbz));
+        int L = 0;
+        while ((int64_t(1) << L) < m) ++L;
+        if (3 * L > 62) BUILD_TRY(fail(GPE_ERR_ARG, "brick grid too large for Morton keys"));
+        E.nkeys = uint64_t(1) << (3 * L);
+    } else {
+        E.nkeys = (uint64_t)nq;
+    }
+    const int64_t nblk = (int64_t)((E.nkeys + ENUM_PER_BLOCK - 1) / ENUM_PER_BLOCK);
+    if (nblk > 0x7fffffffLL) BUILD_TRY(fail(GPE_ERR_ARG, "brick grid too large"));
+    BUILD_TRY(dev_alloc_t(&bsum, nblk));
+    k_enum_count<<<(unsigned)nblk, ENUM_THREADS, 0, st>>>(E, occ, bsum);
+    BUILD_CUDA(cudaGetLastError());
+    std::vector<int64_t> h(nblk);
+    BUILD_CUDA(cudaMemcpyAsync(h.data(), bsum, nblk * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaStreamSynchronize(st));
+    int64_t total = 0;
+    for (int64_t i = 0; i < nblk; ++i) {
+        int64_t c = h[i];
+        h[i] = total;
+        total += c;
+    }
+    if (total == 0) BUILD_TRY(fail(GPE_ERR_ARG, "region of interest is empty (no cell with V < V_cut)"));
+    if (total * g->bc > 0x7fffffffLL * 32LL)
+        BUILD_TRY(fail(GPE_ERR_ARG, "too many stored cells"));
+    g->nb = total;
+    g->n_stored = total * g->bc;
+    BUILD_CUDA(cudaMemcpyAsync(bsum, h.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    BUILD_TRY(dev_alloc_t(&coords, 3 * total));
+    k_enum_emit<<<(unsigned)nblk, ENUM_THREADS, 0, st>>>(E, occ, bsum, coords);
+    BUILD_CUDA(cudaGetLastError());
+
+    BUILD_TRY(dev_alloc_t(&g->d_bvol, nq));
+    BUILD_CUDA(cudaMemsetAsync(g->d_bvol, 0xff, nq * sizeof(int32_t), st));
+    BUILD_TRY(dev_alloc_t(&g->d_org, 3 * total));
+    BUILD_TRY(dev_alloc_t(&g->d_nbr, 6 * total));
+    const unsigned nbb = (unsigned)((total + 255) / 256);
+    k_bricks<<<nbb, 256, 0, st>>>(total, coords, o.bx, o.by, o.bz, g->nbx, g->nby, g->d_bvol, g->d_org);
+    BUILD_CUDA(cudaGetLastError());
+    k_neighbors<<<nbb, 256, 0, st>>>(total, coords, g->nbx, g->nby, g->nbz, g->d_bvol, g->d_nbr);
+    BUILD_CUDA(cudaGetLastError());
+
+    BUILD_TRY(dev_alloc_t(&g->d_mask, g->n_stored / 32));
+    BUILD_TRY(dev_alloc_t(&g->d_V[0], g->n_stored));
+    if (src.mode == 2) {
+        BUILD_TRY(dev_alloc_t(&g->d_V[1], g->n_stored));
+        g->n_slots = 2;
+    }
+    BUILD_TRY(dev_alloc_t(&counters, 2));
+    BUILD_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+    if (total > 0x7fffffffLL) BUILD_TRY(fail(GPE_ERR_ARG, "too many bricks"));
+    k_cells<<<(unsigned)total, std::min(g->bc, 256), 0, st>>>(src, bd, o.bx, o.by, o.bz, o.mask_mode,
+                                                            g->d_org, g->d_V[0], g->d_V[1], g->d_mask,
+                                                            counters, counters + 1);
+    BUILD_CUDA(cudaGetLastError());
+    unsigned long long hc[2];
+    BUILD_CUDA(cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaStreamSynchronize(st));
+    g->n_active = (int64_t)hc[0];
+    long long vb = (long long)hc[1];
+    memcpy(&g->v_max, &vb, sizeof(double));
+    cleanup();
+#undef BUILD_TRY
+#undef BUILD_CUDA
+    *out = g;
+    return GPE_OK;
+}
+
+static int stage_dense(const gpe_box *box, const void *V, int V_dtype, int on_device,
+                       const void **dptr, void **owned, cudaStream_t st)
+{
+    *owned = nullptr;
+    if (!V) return fail(GPE_ERR_ARG, "V is NULL");
+    if (V_dtype != GPE_F64 && V_dtype != GPE_F32) return fail(GPE_ERR_ARG, "V_dtype must be GPE_F64 or GPE_F32");
+    if (on_device) {
+        *dptr = V;
+        return GPE_OK;
+    }
+    size_t bytes = (size_t)box->nx * box->ny * box->nz * (V_dtype == GPE_F64 ? 8 : 4);
+    GPE_TRY(dev_alloc(owned, bytes));
+    cudaError_t e = cudaMemcpyAsync(*owned, V, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        dev_free(*owned);
+        *owned = nullptr;
+        return cuda_fail(e, "cudaMemcpyAsync(V)", __FILE__, __LINE__);
+    }
+    *dptr = *owned;
+    return GPE_OK;
+}
+
+int ensure_vf(gpe_grid *g, int slot)
+{
+    if (g->d_Vf[slot]) return GPE_OK;
+    GPE_TRY(dev_alloc_t(&g->d_Vf[slot], g->n_stored));
+    // conversion is ordered on the legacy stream; synchronise so that any
+    // stream sees the finished copy
+    extern int convert_to_float(const double *src, float *dst, int64_t n);
+    GPE_TRY(convert_to_float(g->d_V[slot], g->d_Vf[slot], g->n_stored));
+    return GPE_OK;
+}
+
+}  // namespace gpe
+
+using namespace gpe;
+
+extern "C" int gpe_grid_create_dense(const gpe_box *box, const void *V, int V_dtype, int V_on_device,
+                                     double V_cut, const gpe_grid_opts *opts, gpe_grid **out,
+                                     gpe_stream stream)
+{
+    if (!out) return fail(GPE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    GPE_TRY(check_box(box));
+    cudaStream_t st = S(stream);
+    const void *dptr = nullptr;
+    void *owned = nullptr;
+    GPE_TRY(stage_dense(box, V, V_dtype, V_on_device, &dptr, &owned, st));
+    VSource src{};
+    src.mode = 0;
+    src.dense = dptr;
+    src.dtype = V_dtype;
+    src.cut0 = V_cut;
+    int rc = build_grid(box, src, opts, out, st);
+    if (owned) {
+        cudaStreamSynchronize(st);
+        dev_free(owned);
+    }
+    return rc;
+}
+
+extern "C" int gpe_grid_create_analytic(const gpe_box *box, const gpe_potential *pot, double V_cut,
+                                        const gpe_grid_opts *opts, gpe_grid **out, gpe_stream stream)
+{
+    if (!out) return fail(GPE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    GPE_TRY(check_box(box));
+    GPE_TRY(check_pot(pot));
+    VSource src{};
+    src.mode = 1;
+    src.p0 = potdesc(*pot);
+    src.cut0 = V_cut;
+    return build_grid(box, src, opts, out, S(stream));
+}
+
+extern "C" int gpe_grid_create_blend(const gpe_box *box, const gpe_potential *pot0, double cut0,
+                                     const gpe_potential *pot1, double cut1, const gpe_grid_opts *opts,
+                                     gpe_grid **out, gpe_stream stream)
+{
+    if (!out) return fail(GPE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    GPE_TRY(check_box(box));
+    GPE_TRY(check_pot(pot0));
+    GPE_TRY(check_pot(pot1));
+    VSource src{};
+    src.mode = 2;
+    src.p0 = potdesc(*pot0);
+    src.p1 = potdesc(*pot1);
+    src.cut0 = cut0;
+    src.cut1 = cut1;
+    return build_grid(box, src, opts, out, S(stream));
+}
+
+extern "C" int gpe_grid_set_potential(gpe_grid *g, int slot, const void *V, int V_dtype, int V_on_device,
+                                      gpe_stream stream)
+{
+    if (!g) return fail(GPE_ERR_ARG, "grid is NULL");
+    if (slot != 0 && slot != 1) return fail(GPE_ERR_ARG, "slot must be 0 or 1");
+    cudaStream_t st = S(stream);
+    const void *dptr = nullptr;
+    void *owned = nullptr;
+    GPE_TRY(stage_dense(&g->box, V, V_dtype, V_on_device, &dptr, &owned, st));
+    int rc = GPE_OK;
+    if (!g->d_V[slot]) rc = dev_alloc_t(&g->d_V[slot], g->n_stored);
+    if (rc == GPE_OK) {
+        k_set_potential<<<(unsigned)g->nb, std::min(g->bc, 256), 0, st>>>(dptr, V_dtype, boxd(g->box), g->bx,
+                                                                        g->by, g->bz, g->d_org, g->d_V[slot]);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "k_set_potential", __FILE__, __LINE__);
+    }
+    if (rc == GPE_OK && slot == 1) g->n_slots = 2;
+    unsigned long long *vb = nullptr;
+    if (rc == GPE_OK) rc = dev_alloc_t(&vb, 1);
+    if (rc == GPE_OK) {
+        cudaMemsetAsync(vb, 0, sizeof(unsigned long long), st);
+        k_vmax<<<g->nsm * 4, 256, 0, st>>>(g->n_stored, g->d_mask, g->d_V[0], g->n_slots > 1 ? g->d_V[1] : nullptr, vb);
+        unsigned long long h = 0;
+        cudaMemcpyAsync(&h, vb, sizeof h, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "set_potential", __FILE__, __LINE__);
+        long long hv = (long long)h;
+        memcpy(&g->v_max, &hv, sizeof(double));
+    }
+    dev_free(vb);
+    if (owned) {
+        cudaStreamSynchronize(st);
+        dev_free(owned);
+    }
+    if (g->d_Vf[slot]) {
+        dev_free(g->d_Vf[slot]);
+        g->d_Vf[slot] = nullptr;
+    }
+    return rc;
+}
+
+extern "C" int gpe_grid_get_info(const gpe_grid *g, gpe_grid_info *out)
+{
+    if (!g || !out) return fail(GPE_ERR_ARG, "NULL argument");
+    out->n_active = g->n_active;
+    out->n_bricks = g->nb;
+    out->n_stored = g->n_stored;
+    out->bx = g->bx;
+    out->by = g->by;
+    out->bz = g->bz;
+    out->mask_mode = g->mask_mode;
+    out->order = g->order;
+    out->n_slots = g->n_slots;
+    out->v_max = g->v_max;
+    out->box = g->box;
+    return GPE_OK;
+}
+
+extern "C" int gpe_grid_bricks(const gpe_grid *g, int32_t *origins, int32_t *nbr)
+{
+    if (!g) return fail(GPE_ERR_ARG, "grid is NULL");
+    if (origins) GPE_TRY_CUDA(cudaMemcpy(origins, g->d_org, g->nb * 3 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (nbr) GPE_TRY_CUDA(cudaMemcpy(nbr, g->d_nbr, g->nb * 6 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return GPE_OK;
+}
+
+extern "C" int gpe_grid_mask(const gpe_grid *g, uint32_t *bits)
+{
+    if (!g || !bits) return fail(GPE_ERR_ARG, "NULL argument");
+    GPE_TRY_CUDA(cudaMemcpy(bits, g->d_mask, g->n_stored / 32 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return GPE_OK;
+}
+
+extern "C" int gpe_grid_potential(const gpe_grid *g, int slot, double *V)
+{
+    if (!g || !V) return fail(GPE_ERR_ARG, "NULL argument");
+    if (slot < 0 || slot > 1 || !g->d_V[slot]) return fail(GPE_ERR_ARG, "potential slot %d not set", slot);
+    GPE_TRY_CUDA(cudaMemcpy(V, g->d_V[slot], g->n_stored * sizeof(double), cudaMemcpyDeviceToHost));
+    return GPE_OK;
+}
+
+extern "C" int gpe_grid_destroy(gpe_grid *g)
+{
+    if (!g) return GPE_OK;
+    if (g->n_states > 0) return fail(GPE_ERR_STATE, "grid still has %d live states", g->n_states);
+    grid_free(g);
+    return GPE_OK;
+}
+
+// ------------------------------------------------------------ Thomas-Fermi mu
+namespace gpe {
+
+// result = {sum over the box of max(mu - V, 0)/g dV, min V, max V}
+__global__ void k_tf_number(VSource src, BoxD box, double mu, double g, double dV, double *partials,
+                            unsigned int *counter, double *result)
+{
+    const int64_t n = box.nx * box.ny * box.nz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    double vmin = 1e300, vmax = -1e300;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = c % box.nx, j = (c / box.nx) % box.ny, k = c / (box.nx * box.ny);
+        double v0, v1;
+        bool sel;
+        cell_values(src, box, i, j, k, v0, v1, sel);
+        if (mu > v0) acc[0] += (mu - v0) / g * dV;
+        vmin = fmin(vmin, v0);
+        vmax = fmax(vmax, v0);
+    }
+    // block min and max of V: reduce them inside the block, then let thread 0
+    // carry them in lanes 1 and 2 of the deterministic reduction so that each
+    // block's values land in partials[b*3 + 1] and partials[b*3 + 2]
+    for (int off = 16; off > 0; off >>= 1) {
+        vmin = fmin(vmin, __shfl_down_sync(0xffffffffu, vmin, off));
+        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, off));
+    }
+    __shared__ double smn[32], smx[32];
+    if ((threadIdx.x & 31) == 0) {
+        smn[threadIdx.x >> 5] = vmin;
+        smx[threadIdx.x >> 5] = vmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w) {
+            smn[0] = fmin(smn[0], smn[w]);
+            smx[0] = fmax(smx[0], smx[w]);
+        }
+    }
+    __syncthreads();
+    acc[1] = threadIdx.x == 0 ? smn[0] : 0.0;
+    acc[2] = threadIdx.x == 0 ? smx[0] : 0.0;
+    double tot[3];
+    if (reduce_finish<3>(acc, partials, counter, tot)) {
+        if (threadIdx.x == 0) {
+            double mn = 1e300, mx = -1e300;
+            for (unsigned b = 0; b < gridDim.x; ++b) {
+                mn = fmin(mn, __ldcg(&partials[b * 3 + 1]));
+                mx = fmax(mx, __ldcg(&partials[b * 3 + 2]));
+            }
+            result[0] = tot[0];
+            result[1] = mn;
+            result[2] = mx;
+        }
+    }
+}
+
+static int tf_mu_impl(const gpe_box *box, const VSource &src, double g, double N, double *mu, cudaStream_t st)
+{
+    if (!(g > 0)) return fail(GPE_ERR_ARG, "g must be > 0 for the Thomas-Fermi estimate");
+    if (!(N > 0)) return fail(GPE_ERR_ARG, "N must be > 0");
+    if (!mu) return fail(GPE_ERR_ARG, "mu is NULL");
+    int dev = 0;
+    GPE_TRY_CUDA(cudaGetDevice(&dev));
+    const int blocks = sm_count(dev) * 4;
+    RedScratch r;
+    GPE_TRY(red_alloc(r, blocks));
+    double *res = nullptr, h[3];
+    int rc = dev_alloc_t(&res, 3);
+    const BoxD bd = boxd(*box);
+    const double dV = box->hx * box->hy * box->hz;
+    auto number = [&](double m, double *out3) -> int {
+        k_tf_number<<<blocks, 256, 0, st>>>(src, bd, m, g, dV, r.partials, r.counter, res);
+        GPE_TRY_CUDA(cudaGetLastError());
+        GPE_TRY_CUDA(cudaMemcpyAsync(out3, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GPE_TRY_CUDA(cudaStreamSynchronize(st));
+        return GPE_OK;
+    };
+    if (rc == GPE_OK) rc = number(0.0, h);
+    if (rc == GPE_OK) {
+        double lo = h[1], hi = h[2];
+        double span = hi - lo > 0 ? hi - lo : 1.0;
+        for (int it = 0; it < 200 && rc == GPE_OK; ++it) {
+            rc = number(hi, h);
+            if (rc != GPE_OK || h[0] >= N) break;
+            hi += span;
+            span *= 2.0;
+        }
+        for (int it = 0; it < 200 && rc == GPE_OK; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            rc = number(mid, h);
+            if (rc != GPE_OK) break;
+            if (h[0] < N) lo = mid; else hi = mid;
+        }
+        *mu = 0.5 * (lo + hi);
+    }
+    dev_free(res);
+    red_free(r);
+    return rc;
+}
+
+}  // namespace gpe
+
+extern "C" int gpe_tf_mu_dense(const gpe_box *box, const void *V, int V_dtype, int V_on_device, double g,
+                               double N, double *mu, gpe_stream stream)
+{
+    GPE_TRY(check_box(box));
+    cudaStream_t st = S(stream);
+    const void *dptr = nullptr;
+    void *owned = nullptr;
+    GPE_TRY(stage_dense(box, V, V_dtype, V_on_device, &dptr, &owned, st));
+    VSource src{};
+    src.mode = 0;
+    src.dense = dptr;
+    src.dtype = V_dtype;
+    src.cut0 = 0.0;
+    int rc = tf_mu_impl(box, src, g, N, mu, st);
+    if (owned) {
+        cudaStreamSynchronize(st);
+        dev_free(owned);
+    }
+    return rc;
+}
+
+extern "C" int gpe_tf_mu_analytic(const gpe_box *box, const gpe_potential *pot, double g, double N, double *mu,
+                                  gpe_stream stream)
+{
+    GPE_TRY(check_box(box));
+    GPE_TRY(check_pot(pot));
+    VSource src{};
+    src.mode = 1;
+    src.p0 = potdesc(*pot);
+    return tf_mu_impl(box, src, g, N, mu, S(stream));
+}

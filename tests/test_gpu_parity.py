@@ -1,0 +1,356 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (derived from the arithmetic):
+  * complex128 path: relative L2 <= 1e-12 per step (the oracle and the kernels
+    evaluate the same expressions in FP64; only rounding order differs, ~1e-16
+    per operation, amplified by at most dt*||H|| ~ 0.2 per step);
+  * complex64 path: FP32 round-off of a handful of operations per stage,
+    ~6e-8 each: relative L2 <= 2e-6 after one step, <= 1e-5 after 10 steps;
+  * integer work (masks, tables, counts) is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_05447_gb300 import gpe, inputs
+
+from gpu_cases import harmonic64, shell, ragged_shell, single_cell, ramp_case, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C128_TOL = 1e-12
+C64_TOL_1 = 2e-6
+C64_TOL_10 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2603_05447_gb300 import _build
+    _build.build()
+    torch.cuda.init()
+    torch.cuda.set_device(0)
+    return gpe.load()
+
+
+class Gpu:
+    """Grid + state for a case (destroyed on exit)."""
+
+    def __init__(self, case, dtype=gpe.GPE_C128, brick=(8, 8, 8), order=gpe.GPE_ORDER_MORTON,
+                 mask_mode=gpe.GPE_MASK_CELL):
+        opts = gpe.make_opts(brick, mask_mode, order)
+        if case.V1 is None:
+            self.grid = gpe.gpe_grid_create_dense(case.gbox, case.V, case.V_cut, opts)
+        else:
+            ind = np.where(case.region, -1.0, 1.0)
+            self.grid = gpe.gpe_grid_create_dense(case.gbox, ind, 0.0, opts)
+            gpe.gpe_grid_set_potential(self.grid, 0, case.V)
+            gpe.gpe_grid_set_potential(self.grid, 1, case.V1)
+        self.dtype = dtype
+        self.state = gpe.gpe_state_create(self.grid, dtype)
+        self.case = case
+        self.load(case.psi)
+
+    def load(self, psi):
+        arr = np.ascontiguousarray(psi, dtype=np.complex128 if self.dtype == gpe.GPE_C128 else np.complex64)
+        gpe.gpe_state_load(self.state, arr, gpe.GPE_LAYOUT_DENSE)
+
+    def dense(self):
+        out = np.zeros(self.case.box.shape, np.complex128 if self.dtype == gpe.GPE_C128 else np.complex64)
+        gpe.gpe_state_store(self.state, out, gpe.GPE_LAYOUT_DENSE)
+        return out.astype(np.complex128)
+
+    def close(self):
+        gpe.gpe_state_destroy(self.state)
+        gpe.gpe_grid_destroy(self.grid)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def oracle_grid(case):
+    mask = case.mask if case.V1 is None else case.region
+    return oracle.Grid(mask, (case.box.hx, case.box.hy, case.box.hz))
+
+
+# ----------------------------------------------------------------- grid builder
+def morton_key(c):
+    key = 0
+    for bit in range(21):
+        for ax in range(3):
+            key |= ((int(c[ax]) >> bit) & 1) << (3 * bit + ax)
+    return key
+
+
+@pytest.mark.parametrize("brick", [(8, 8, 8), (8, 8, 4), (8, 4, 4), (4, 4, 4)])
+@pytest.mark.parametrize("order", [gpe.GPE_ORDER_MORTON, gpe.GPE_ORDER_ZMAJOR])
+def test_grid_mask_tables_and_order(brick, order):
+    case = ragged_shell()
+    with Gpu(case, brick=brick, order=order) as G:
+        info = gpe.gpe_grid_get_info(G.grid)
+        assert info.n_active == int(case.mask.sum())
+        org, nbr = gpe.gpe_grid_bricks(G.grid)
+        bits = gpe.gpe_grid_mask(G.grid)
+        bx, by, bz = brick
+        assert info.n_stored == info.n_bricks * bx * by * bz
+        # active bits -> dense active set, exactly V < V_cut
+        slots = np.flatnonzero(np.unpackbits(bits.view(np.uint8), bitorder="little"))
+        b, l = slots // (bx * by * bz), slots % (bx * by * bz)
+        i = org[b, 0] + l % bx
+        j = org[b, 1] + (l // bx) % by
+        k = org[b, 2] + l // (bx * by)
+        dense = np.zeros(case.box.shape, bool)
+        dense[k, j, i] = True
+        assert np.array_equal(dense, case.mask)
+        # every brick holding an active cell is present, and only those
+        bc = org // np.array(brick)
+        occ = set(map(tuple, np.argwhere(case.mask)[:, ::-1] // np.array(brick)))
+        assert set(map(tuple, bc)) == occ
+        # neighbour table against brute force
+        pos = {tuple(c): n for n, c in enumerate(bc)}
+        for n, c in enumerate(bc):
+            for d in range(6):
+                q = list(c)
+                q[d // 2] += 1 if d % 2 else -1
+                assert nbr[n, d] == pos.get(tuple(q), -1)
+        keys = [morton_key(c) if order == gpe.GPE_ORDER_MORTON else
+                c[0] + 1000 * (c[1] + 1000 * c[2]) for c in bc]
+        assert all(a < b for a, b in zip(keys, keys[1:]))
+
+
+def test_brick_mask_mode_selects_whole_bricks():
+    case = ragged_shell()
+    with Gpu(case, mask_mode=gpe.GPE_MASK_BRICK) as G:
+        info = gpe.gpe_grid_get_info(G.grid)
+        bb = np.zeros(case.box.shape, bool)
+        sel = np.argwhere(case.mask)[:, ::-1] // 8
+        for cx, cy, cz in set(map(tuple, sel)):
+            bb[cz * 8:cz * 8 + 8, cy * 8:cy * 8 + 8, cx * 8:cx * 8 + 8] = True
+        assert info.n_active == int(bb.sum())
+
+
+def test_analytic_builder_matches_dense_samples():
+    wl = inputs.SHELL_64
+    box = wl.box
+    gb = gpe.make_box(box.nx, box.ny, box.nz, box.hx)
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    ga = gpe.gpe_grid_create_analytic(gb, pot, wl.V_cut)
+    V = inputs.dense_potential(box, wl.potential)
+    gd = gpe.gpe_grid_create_dense(gb, V, wl.V_cut)
+    try:
+        ia, id_ = gpe.gpe_grid_get_info(ga), gpe.gpe_grid_get_info(gd)
+        near = np.abs(V - wl.V_cut) < 1e-9 * wl.V_cut
+        assert abs(ia.n_active - id_.n_active) <= int(near.sum())
+        Va, Vd = gpe.gpe_grid_potential(ga), gpe.gpe_grid_potential(gd)
+        if ia.n_bricks == id_.n_bricks:
+            assert np.allclose(Va, Vd, rtol=1e-13, atol=1e-12 * wl.V_cut)
+    finally:
+        gpe.gpe_grid_destroy(ga)
+        gpe.gpe_grid_destroy(gd)
+
+
+def test_empty_region_and_destroy_order_errors():
+    case = single_cell()
+    with pytest.raises(gpe.GpeError) as e:
+        gpe.gpe_grid_create_dense(case.gbox, case.V, -1.0)
+    assert e.value.code == gpe.GPE_ERR_ARG
+    G = Gpu(case)
+    with pytest.raises(gpe.GpeError) as e:
+        gpe.gpe_grid_destroy(G.grid)
+    assert e.value.code == gpe.GPE_ERR_STATE
+    G.close()
+
+
+# ----------------------------------------------------------------- load / store
+@pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64])
+def test_load_store_roundtrip_is_exact(dtype):
+    case = ragged_shell()
+    with Gpu(case, dtype=dtype) as G:
+        out = G.dense()
+        want = np.where(case.mask, case.psi, 0)
+        if dtype == gpe.GPE_C64:
+            want = want.astype(np.complex64).astype(np.complex128)
+        assert np.array_equal(out, want)
+        info = gpe.gpe_grid_get_info(G.grid)
+        cdt = np.complex128 if dtype == gpe.GPE_C128 else np.complex64
+        comp = np.zeros(info.n_stored, cdt)
+        gpe.gpe_state_store(G.state, comp, gpe.GPE_LAYOUT_COMPACT)
+        junk = comp + (1.0 + 2.0j)       # inactive slots must be forced to zero on load
+        gpe.gpe_state_load(G.state, np.ascontiguousarray(junk), gpe.GPE_LAYOUT_COMPACT)
+        back = G.dense()
+        assert np.array_equal(np.where(case.mask, back, 0), back)
+        shifted = (out.astype(cdt) + (1.0 + 2.0j)).astype(np.complex128)   # same rounding as junk
+        assert np.array_equal(back[case.mask], shifted[case.mask])
+
+
+# ----------------------------------------------------------------- real time
+CASES = {"harmonic64": harmonic64, "shell64": shell, "ragged": ragged_shell, "single": single_cell}
+
+
+def oracle_rk4(case, og, psi, nsteps, t0=0.0):
+    V = og.compact(case.V)
+    y = og.compact(psi)
+    for q in range(nsteps):
+        if case.V1 is None:
+            y = oracle.rk4_step(og, V, y, case.g, t0 + q * case.dt, case.dt)
+        else:
+            y = oracle.rk4_step(og, V, y, case.g, t0 + q * case.dt, case.dt, og.compact(case.V1),
+                                case.knots, case.T)
+    return og.dense(y)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("nsteps", [1, 10])
+def test_rk4_c128_matches_oracle(name, nsteps):
+    case = CASES[name]()
+    og = oracle_grid(case)
+    ref = oracle_rk4(case, og, case.psi, nsteps)
+    with Gpu(case) as G:
+        gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), nsteps)
+        assert rel_l2(G.dense(), ref) <= C128_TOL
+
+
+@pytest.mark.parametrize("brick", [(8, 8, 4), (8, 4, 4), (4, 4, 4)])
+def test_rk4_c128_other_brick_shapes(brick):
+    case = ragged_shell()
+    og = oracle_grid(case)
+    ref = oracle_rk4(case, og, case.psi, 3)
+    with Gpu(case, brick=brick, order=gpe.GPE_ORDER_ZMAJOR) as G:
+        gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), 3)
+        assert rel_l2(G.dense(), ref) <= C128_TOL
+
+
+@pytest.mark.parametrize("name", ["harmonic64", "ragged"])
+def test_rk4_c64_matches_oracle(name):
+    case = CASES[name]()
+    og = oracle_grid(case)
+    with Gpu(case, dtype=gpe.GPE_C64) as G:
+        psi32 = G.dense()                      # the complex64-rounded input
+        gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), 1)
+        assert rel_l2(G.dense(), oracle_rk4(case, og, psi32, 1)) <= C64_TOL_1
+        gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), 9)
+        assert rel_l2(G.dense(), oracle_rk4(case, og, psi32, 10)) <= C64_TOL_10
+
+
+def test_rk4_ramp_blend_matches_oracle():
+    case = ramp_case()
+    og = oracle_grid(case)
+    t0 = 7 * case.dt
+    ref = oracle_rk4(case, og, case.psi, 12, t0=t0)
+    with Gpu(case) as G:
+        p = gpe.real_params(case.g, case.dt, gpe.GPE_V_BLEND, case.knots, case.T)
+        gpe.gpe_step_real(G.state, p, 12, t0)
+        assert rel_l2(G.dense(), ref) <= C128_TOL
+
+
+def test_rk4_rejects_unstable_dt():
+    case = harmonic64()
+    with Gpu(case) as G:
+        with pytest.raises(gpe.GpeError) as e:
+            gpe.gpe_step_real(G.state, gpe.real_params(case.g, 0.05), 1)
+        assert e.value.code == gpe.GPE_ERR_UNSTABLE
+        gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), 0)   # zero steps: no-op
+        assert np.array_equal(G.dense(), case.psi)
+
+
+# ----------------------------------------------------------------- imaginary time
+def oracle_itp(case, og, psi, nsteps):
+    V = og.compact(case.V)
+    y = og.compact(psi)
+    for _ in range(nsteps):
+        y, _ = oracle.itp_step(og, V, y, case.g, case.dt, 1.0)
+    return og.dense(y)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("nsteps", [1, 20])
+def test_itp_c128_matches_oracle(name, nsteps):
+    case = CASES[name]()
+    og = oracle_grid(case)
+    ref = oracle_itp(case, og, case.psi, nsteps)
+    with Gpu(case) as G:
+        gpe.gpe_step_imag(G.state, gpe.gpe_imag_params(case.g, case.dt, 1.0), nsteps)
+        assert rel_l2(G.dense(), ref) <= C128_TOL
+
+
+def test_itp_c64_matches_oracle():
+    case = shell()
+    og = oracle_grid(case)
+    with Gpu(case, dtype=gpe.GPE_C64) as G:
+        psi32 = G.dense()
+        gpe.gpe_step_imag(G.state, gpe.gpe_imag_params(case.g, case.dt, 1.0), 10)
+        assert rel_l2(G.dense(), oracle_itp(case, og, psi32, 10)) <= C64_TOL_10
+
+
+def test_ground_state_harmonic_g0_energy():
+    """g = 0, 64^3, h = 0.25: E -> 3 lambda_min(1D) = 1.4941174639 up to the
+    O(dt^2) splitting bias of the ITP fixed point."""
+    case = harmonic64(g=0.0)
+    with Gpu(case) as G:
+        p = gpe.gpe_imag_params(0.0, 1e-3, 1.0)
+        steps, obs = gpe.gpe_ground_state(G.state, p, 1e-12, 500, 60000)
+        assert abs(obs["energy"] - 1.4941174639) < 2e-6
+        assert abs(obs["mu"] - obs["energy"]) < 1e-9
+        assert abs(obs["norm"] - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------- observables
+@pytest.mark.parametrize("name", ["harmonic64", "ragged"])
+@pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64])
+def test_observables_match_oracle(name, dtype):
+    case = CASES[name]()
+    og = oracle_grid(case)
+    with Gpu(case, dtype=dtype) as G:
+        psi = G.dense()
+        ref = oracle.observables(og, og.compact(case.V), case.g, og.compact(psi))
+        got = gpe.gpe_observables(G.state, case.g)
+        tol = 1e-12 if dtype == gpe.GPE_C128 else 2e-6
+        for k in ("norm", "energy", "mu", "e_kin", "e_pot", "e_int"):
+            assert abs(got[k] - ref[k]) <= tol * max(abs(ref[k]), 1e-300) + 1e-300, (k, got[k], ref[k])
+        assert got["nonfinite"] == 0
+
+
+def test_observables_report_nonfinite():
+    case = ragged_shell()
+    psi = case.psi.copy()
+    idx = np.argwhere(case.mask)[:3]
+    for k, j, i in idx:
+        psi[k, j, i] = np.nan
+    with Gpu(case) as G:
+        G.load(psi)
+        with pytest.raises(gpe.GpeError) as e:
+            gpe.gpe_observables(G.state, case.g)
+        assert e.value.code == gpe.GPE_ERR_NONFINITE
+        assert gpe.gpe_observables(G.state, case.g, check=False)["nonfinite"] == 3
+
+
+def test_overlap_matches_oracle():
+    case = ragged_shell()
+    og = oracle_grid(case)
+    with Gpu(case) as A:
+        B = gpe.gpe_state_create(A.grid, gpe.GPE_C128)
+        try:
+            other = inputs.random_state(case.box.shape, seed=9)
+            gpe.gpe_state_load(B, np.ascontiguousarray(other), gpe.GPE_LAYOUT_DENSE)
+            got = gpe.gpe_overlap(A.state, B)
+            ref = oracle.overlap(og.compact(case.psi), og.compact(other), og.dV)
+            assert abs(got - ref) <= 1e-12 * abs(ref)
+        finally:
+            gpe.gpe_state_destroy(B)
+
+
+def test_tf_mu_matches_oracle():
+    box = inputs.cubic_box(80, 0.1)
+    V = inputs.dense_potential(box, inputs.Harmonic())
+    gb = gpe.make_box(80, 80, 80, 0.1)
+    mu_gpu = gpe.gpe_tf_mu_dense(gb, V, 500.0, 1.0)
+    mu_orc = oracle.tf_mu(V, box.dV, 500.0, 1.0)
+    assert abs(mu_gpu - mu_orc) <= 1e-10 * mu_orc
+    pot = gpe.make_potential(gpe.GPE_POT_HARMONIC, 1, 1, 1)
+    mu_an = gpe.gpe_tf_mu_analytic(gb, pot, 500.0, 1.0)
+    assert abs(mu_an - mu_orc) <= 1e-10 * mu_orc
