@@ -1,0 +1,412 @@
+"""Benchmark: active-cell-steps/s of the real-time RK4 GPE step on the
+anisotropic thin-shell workload (1024^3 box, ~2.9e7 active cells, g = 2000),
+complex64 bulk with FP64 reductions, on one GB300; complex128 reported beside.
+
+One bench step = STEPS_PER_BENCH (100) RK4 time steps over the whole active
+set plus one FP64 observables reduction (norm, energy, mu).  Inputs (state,
+potential, masks) are larger than L2 and already resident when timing starts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the single-shell step
+has no data-parallel exchange); value = cell-steps of all ranks / max time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a slab of the shell).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEPS_PER_BENCH = 100
+B_ALG = {"c64": 20.0, "c128": 40.0}   # algorithmic bytes per active cell-step (read psi, V; write psi)
+METRIC = "shell-grid GPE cell-steps/s: FP32 vs FP64 at stated error; % of HBM roofline"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rk4_shell1024_c64_traffic.json")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_05447_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.out = index, None, ""
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(", ") for r in self.out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- workload
+WORKLOADS = {"shell1024": "SHELL_1024", "shell512": "SHELL_512"}
+_workload_name = "shell1024"
+
+
+def shell_workload():
+    from paper_2603_05447_gb300 import inputs
+    return getattr(inputs, WORKLOADS[_workload_name])
+
+
+def build_grid(gpe, wl, brick=(8, 8, 8)):
+    b = wl.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    return gpe.gpe_grid_create_analytic(gb, pot, wl.V_cut, gpe.make_opts(brick))
+
+
+def initial_compact(gpe, inputs, wl, grid):
+    """Shell profile with smooth seeded phase noise at every stored slot."""
+    info = gpe.gpe_grid_get_info(grid)
+    org, _ = gpe.gpe_grid_bricks(grid)
+    bx, by, bz = info.bx, info.by, info.bz
+    l = np.arange(bx * by * bz)
+    b = wl.box
+    out = np.empty(info.n_stored, np.complex128)
+    step = 8192
+    for s in range(0, org.shape[0], step):
+        o = org[s:s + step]
+        x = b.x0 + (o[:, 0:1] + l % bx).ravel() * b.hx
+        y = b.y0 + (o[:, 1:2] + (l // bx) % by).ravel() * b.hy
+        z = b.z0 + (o[:, 2:3] + l // (bx * by)).ravel() * b.hz
+        out[s * bx * by * bz:(s + o.shape[0]) * bx * by * bz] = inputs.shell_initial_psi(wl, x, y, z)
+    bits = gpe.gpe_grid_mask(grid)
+    active = np.unpackbits(bits.view(np.uint8), bitorder="little").astype(bool)
+    out[~active] = 0
+    out *= math.sqrt(wl.N / (np.sum(np.abs(out) ** 2) * b.dV))
+    return out
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+def oracle_sample(wl, target_s=12.0, layers=48):
+    """A slab of `layers` z-planes through the shell's equator: (grid, V, psi)."""
+    import oracle
+    from paper_2603_05447_gb300 import inputs
+    b = wl.box
+    x, y, z = b.axes()
+    k0 = b.nz // 2 - layers // 2
+    zs = z[k0:k0 + layers]
+    Z, Y, X = np.meshgrid(zs, y, x, indexing="ij")
+    V = wl.potential(X, Y, Z)
+    mask = V < wl.V_cut
+    g = oracle.Grid(mask, b.hx)
+    xc, yc, zc = X[mask], Y[mask], Z[mask]
+    psi = inputs.shell_initial_psi(wl, xc, yc, zc)
+    psi *= math.sqrt(1.0 / (np.sum(np.abs(psi) ** 2) * b.dV))
+    return g, g.compact(V), psi
+
+
+def cpu_baseline(wl, target_s=12.0):
+    import oracle
+    g, V, psi = oracle_sample(wl)
+    dt = wl.stable_dt()
+    t0 = time.perf_counter()
+    y = oracle.rk4_step(g, V, psi, wl.g, 0.0, dt)
+    one = time.perf_counter() - t0
+    n = max(1, int(target_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    for q in range(n):
+        y = oracle.rk4_step(g, V, y, wl.g, (q + 1) * dt, dt)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": g.n * n / el, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle RK4, {n} steps on a {g.n}-cell slab (48 z-planes through the "
+                      f"equator) of the same shell, {el:.1f} s"}
+
+
+# ----------------------------------------------------------------- ranks
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(world, x):
+    import torch
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- our arm
+def time_rk4(gpe, torch, st, params, steps, warmup, n_active, g):
+    """Warm up, then time `steps` bench steps; returns (ms per bench step,
+    ms per RK4 step of the stage kernels alone)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        gpe.gpe_step_real(st, params, STEPS_PER_BENCH)
+        gpe.gpe_observables(st, g)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        gpe.gpe_step_real(st, params, STEPS_PER_BENCH)
+        e1.record(stream)
+        gpe.gpe_observables(st, g)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    total = sum(e0.elapsed_time(e2) for e0, _, e2 in ev)
+    rk = sum(e0.elapsed_time(e1) for e0, e1, _ in ev)
+    return total, rk / (steps * STEPS_PER_BENCH)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    from paper_2603_05447_gb300 import _build, gpe, inputs
+    if rank == 0 or world > 1:
+        _build.build()
+    barrier(world)
+    gpe.load()
+    wl = shell_workload()
+    grid = build_grid(gpe, wl)
+    info = gpe.gpe_grid_get_info(grid)
+    n_active, n_stored = info.n_active, info.n_stored
+    psi0 = initial_compact(gpe, inputs, wl, grid)
+    dt = wl.stable_dt()
+    params = gpe.real_params(wl.g, dt)
+
+    st64 = gpe.gpe_state_create(grid, gpe.GPE_C64)
+    psi64 = np.ascontiguousarray(psi0.astype(np.complex64))
+    gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
+
+    # ---- device-resident timing (complex64, the headline)
+    barrier(world)
+    launches0 = gpe.gpe_launch_count()
+    with ClockSampler(local) as clk:
+        total_ms, rk_ms = time_rk4(gpe, torch, st64, params, args.steps, args.warmup, n_active, wl.g)
+    launches = gpe.gpe_launch_count() - launches0
+    per_warm = (launches // (args.steps + args.warmup))
+    gpu_launches = per_warm * args.steps
+    barrier(world)
+    total_ms = max_over_ranks(world, total_ms)
+    cell_steps = n_active * STEPS_PER_BENCH * args.steps * world
+    value = cell_steps / (total_ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    achieved = B_ALG["c64"] * n_active / (rk_ms / 1e3) / 1e9
+
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        t = json.load(open(TRAFFIC_FILE))
+        if t.get("kernel_source_hash") == kernel_source_hash():
+            traffic = t.get("bytes_per_step")
+
+    if args.quick:
+        gpe.gpe_state_destroy(st64)
+        gpe.gpe_grid_destroy(grid)
+        if rank == 0:
+            print(json.dumps({"quick": True, "workload": _workload_name, "value": value,
+                              "ms_per_rk4_step": rk_ms, "achieved_gbs": achieved, "n_active": n_active,
+                              "gpu_launches": gpu_launches}), flush=True)
+        return
+
+    # ---- end to end: host buffers through the C ABI, copies inside the timed region
+    pinned_in = torch.empty(n_stored, dtype=torch.complex64, pin_memory=True)
+    pinned_out = torch.empty(n_stored, dtype=torch.complex64, pin_memory=True)
+    pinned_in.numpy()[:] = psi64
+    gpe.gpe_state_load(st64, pinned_in.numpy(), gpe.GPE_LAYOUT_COMPACT)
+    e2e_steps = max(2, min(args.steps, 3))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gpe.gpe_state_load(st64, pinned_in.numpy(), gpe.GPE_LAYOUT_COMPACT)
+        gpe.gpe_step_real(st64, params, STEPS_PER_BENCH)
+        gpe.gpe_state_store(st64, pinned_out.numpy(), gpe.GPE_LAYOUT_COMPACT)
+        gpe.gpe_observables(st64, wl.g)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = n_active * STEPS_PER_BENCH * e2e_steps * world / e2e_s
+
+    # ---- complex128 path and the FP32-vs-FP64 error after the same steps
+    st128 = gpe.gpe_state_create(grid, gpe.GPE_C128)
+    gpe.gpe_state_load(st128, np.ascontiguousarray(psi0), gpe.GPE_LAYOUT_COMPACT)
+    gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
+    n128 = max(1, min(args.steps, 2))
+    t128_ms, rk128_ms = time_rk4(gpe, torch, st128, params, n128, 1, n_active, wl.g)
+    fp64_value = n_active * STEPS_PER_BENCH * n128 * world / (max_over_ranks(world, t128_ms) / 1e3)
+    gpe.gpe_step_real(st64, params, STEPS_PER_BENCH * (n128 + 1))
+    a = np.empty(n_stored, np.complex64)
+    c = np.empty(n_stored, np.complex128)
+    gpe.gpe_state_store(st64, a, gpe.GPE_LAYOUT_COMPACT)
+    gpe.gpe_state_store(st128, c, gpe.GPE_LAYOUT_COMPACT)
+    err = float(np.linalg.norm(a.astype(np.complex128) - c) / np.linalg.norm(c))
+    o64 = gpe.gpe_observables(st64, wl.g)
+    o128 = gpe.gpe_observables(st128, wl.g)
+
+    gpe.gpe_state_destroy(st64)
+    gpe.gpe_state_destroy(st128)
+    gpe.gpe_grid_destroy(grid)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "anisotropic thin ellipsoidal shell, 1024^3 box, semi-axes 490/441/392 cells, "
+                               "g=2000, N=1, mask V<5mu0, RK4 real time, complex64 bulk + FP64 reductions",
+                   "n_active": n_active, "n_stored": n_stored, "brick": f"{info.bx}x{info.by}x{info.bz}",
+                   "rk4_steps_per_bench_step": STEPS_PER_BENCH, "dt": dt,
+                   "l2": "inputs larger than L2 (state %.0f MB + potential %.0f MB)" % (n_stored * 8 / 1e6, n_stored * 4 / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "RK4 step (k_rk4 stage kernels)", "peak_kind": peak_kind,
+                     "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms},
+        "fp64": {"value": fp64_value, "unit": "cell-steps/s", "ms_per_rk4_step": rk128_ms,
+                 "fp32_over_fp64": value / fp64_value,
+                 "rel_l2_fp32_vs_fp64": err, "steps_compared": STEPS_PER_BENCH * (n128 + 1),
+                 "norm_fp32": o64["norm"], "norm_fp64": o128["norm"]},
+        "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": n_stored * 8,
+                "d2h_bytes_per_step": n_stored * 8 + 7 * 8},
+        "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+    }
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = shell_workload()
+    g, V, psi = oracle_sample(wl)
+    dt = wl.stable_dt()
+    y = psi
+    for q in range(args.warmup):
+        y = oracle.rk4_step(g, V, y, wl.g, q * dt, dt)
+    times = []
+    for q in range(args.steps):
+        t0 = time.perf_counter()
+        y = oracle.rk4_step(g, V, y, wl.g, q * dt, dt)
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = g.n * args.steps / el
+    sample = (f"FP64 oracle RK4 on a {g.n}-cell slab (48 z-planes through the equator) of the "
+              f"same shell, one RK4 step per bench step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "anisotropic thin ellipsoidal shell, 1024^3 box, semi-axes 490/441/392 "
+                                   "cells, g=2000 (bounded CPU sample)", "n_active_sample": g.n},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="shell1024",
+                    help="shell512 is the smaller case used for ncu captures")
+    ap.add_argument("--quick", action="store_true",
+                    help="device-resident complex64 timing only (for profiling runs)")
+    args = ap.parse_args()
+    global _workload_name
+    _workload_name = args.workload
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,11 @@ int gpe_version(void);
  * truncated to n bytes).  Returns the length of the full message. */
 int gpe_last_error(char *buf, size_t n);
 
+/* Number of CUDA kernels this library has launched in this process
+ * (diagnostics; counts enqueued launches, including those captured into
+ * CUDA graphs at capture time only). */
+int gpe_launch_count(uint64_t *out);
+
 /* ------------------------------------------------------------------ grids */
 /* Cartesian bounding box.  (x0, y0, z0) is the centre of cell (0, 0, 0). */
 typedef struct gpe_box {

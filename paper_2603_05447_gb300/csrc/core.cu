@@ -1,4 +1,5 @@
 // core.cu -- error reporting, allocation and small utilities of libgpeshell.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <string>
@@ -8,6 +9,9 @@
 namespace gpe {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int fail(int code, const char *fmt, ...)
 {
@@ -99,6 +103,13 @@ int launch_blocks(const gpe_grid *g, int threads, int per_sm)
 }  // namespace gpe
 
 extern "C" int gpe_version(void) { return 100; }
+
+extern "C" int gpe_launch_count(uint64_t *out)
+{
+    if (!out) return gpe::fail(GPE_ERR_ARG, "out is NULL");
+    *out = (uint64_t)gpe::g_launches.load(std::memory_order_relaxed);
+    return GPE_OK;
+}
 
 extern "C" int gpe_last_error(char *buf, size_t n)
 {

@@ -36,7 +36,14 @@ int cuda_fail(cudaError_t e, const char *expr, const char *file, int line);
         int r__ = (x);                                                       \
         if (r__ != GPE_OK) return r__;                                       \
     } while (0)
-#define GPE_LAUNCH_CHECK() GPE_TRY_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by GPE_LAUNCH_CHECK(), which
+// also counts it (gpe_launch_count)
+void count_launch();
+#define GPE_LAUNCH_CHECK()                                                   \
+    do {                                                                     \
+        ::gpe::count_launch();                                               \
+        GPE_TRY_CUDA(cudaGetLastError());                                    \
+    } while (0)
 
 int dev_alloc(void **p, size_t bytes);
 template <typename T>

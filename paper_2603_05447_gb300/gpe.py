@@ -96,6 +96,7 @@ _P = C.c_void_p
 _SIGS = {
     "gpe_version": (C.c_int, []),
     "gpe_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "gpe_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
     "gpe_grid_create_dense": (C.c_int, [C.POINTER(gpe_box), _P, C.c_int, C.c_int, C.c_double,
                                         C.POINTER(gpe_grid_opts), C.POINTER(_P), _P]),
     "gpe_grid_create_analytic": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.c_double,
@@ -250,6 +251,12 @@ def real_params(g, dt, potential=GPE_V_STATIC, knots=None, T_ramp=0.0) -> gpe_re
 # ----------------------------------------------------------------- C ABI, same names
 def gpe_version() -> int:
     return load().gpe_version()
+
+
+def gpe_launch_count() -> int:
+    n = C.c_uint64()
+    _check(load().gpe_launch_count(C.byref(n)))
+    return n.value
 
 
 def gpe_grid_create_dense(box, V, V_cut, opts=None, stream=None):
