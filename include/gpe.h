@@ -271,6 +271,26 @@ int gpe_observables(const gpe_state *st, double g, double s_blend,
 int gpe_overlap(const gpe_state *a, const gpe_state *b, double out[2],
                 gpe_stream stream);
 
+/* Overlap <a|b> = sum conj(a) b dV of two caller-owned device arrays of n
+ * complex values (dtype GPE_C128 or GPE_C64), for callers that cannot
+ * allocate device memory when they need the result: for example a host
+ * application whose memory pool already holds the device's free memory, or a
+ * loop that must not call cudaMalloc/cudaFree (they can synchronise the device
+ * and stall other streams).  The paper has no counterpart; it is a service of
+ * this library.  Entries of a and b outside the region of interest must be
+ * zero (as in a state's compact array, see gpe_state_device_ptr).
+ * Allocates nothing: the per-block FP64 partial sums live in a fixed array of
+ * 512 KiB compiled into the library, which every GPU that loads the library
+ * keeps until the process exits.  Limit: n <= 268,435,456 (one reduction block
+ * per 8192 elements, at most 32768 blocks); larger n returns GPE_ERR_ARG.  The
+ * first call on each device looks up that array's device address, so make it
+ * before capturing any stream.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Writes out[0..1] (re, im) on the host;
+ * synchronous. */
+int gpe_overlap_noalloc(const void *a, const void *b, int64_t n, int dtype,
+                        double dV, double out[2], gpe_stream stream);
+
 /* Imaginary-time ground state (Sec. III: iterate to a tolerance): gpe_step_imag
  * in blocks of check_every steps until |mu_n - mu_{n-1}| < tol_dmu between two
  * checks.  *steps_done and *obs (may be NULL) report the last check.

@@ -124,6 +124,7 @@ _SIGS = {
     "gpe_step_real": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, _P]),
     "gpe_observables": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(gpe_obs), _P]),
     "gpe_overlap": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P]),
+    "gpe_overlap_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_double), _P]),
     "gpe_ground_state": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_double, C.c_int64, C.c_int64,
                                    C.POINTER(C.c_int64), C.POINTER(gpe_obs), _P]),
 }
@@ -382,6 +383,16 @@ def gpe_observables(state, g, s_blend=0.0, stream=None, check=True) -> dict:
 def gpe_overlap(a, b, stream=None) -> complex:
     out = (C.c_double * 2)()
     _check(load().gpe_overlap(a, b, out, stream_handle(stream)))
+    return complex(out[0], out[1])
+
+
+def gpe_overlap_noalloc(a, b, n, dtype, dV, stream=None) -> complex:
+    """Overlap of two device arrays (pointers or CUDA tensors) without any
+    device allocation (see include/gpe.h for the limit and sharing rules)."""
+    pa, _ = pointer(a)
+    pb, _ = pointer(b)
+    out = (C.c_double * 2)()
+    _check(load().gpe_overlap_noalloc(pa, pb, int(n), int(dtype), float(dV), out, stream_handle(stream)))
     return complex(out[0], out[1])
 
 
