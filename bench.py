@@ -111,31 +111,24 @@ def shell_workload():
     return getattr(inputs, WORKLOADS[_workload_name])
 
 
-def build_grid(gpe, wl, brick=(8, 8, 8)):
+def build_grid(gpe, wl, brick=(8, 8, 8), sched=0, chunk=0):
     b = wl.box
     gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
     pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
-    return gpe.gpe_grid_create_analytic(gb, pot, wl.V_cut, gpe.make_opts(brick))
+    return gpe.gpe_grid_create_analytic(gb, pot, wl.V_cut, gpe.make_opts(brick, sched=sched, chunk=chunk))
 
 
 def initial_compact(gpe, inputs, wl, grid):
-    """Shell profile with smooth seeded phase noise at every stored slot."""
+    """Shell profile with smooth seeded phase noise at every active cell, in
+    the compact layout."""
     info = gpe.gpe_grid_get_info(grid)
-    org, _ = gpe.gpe_grid_bricks(grid)
-    bx, by, bz = info.bx, info.by, info.bz
-    l = np.arange(bx * by * bz)
+    idx, i, j, k = gpe.packed_coords(grid)
     b = wl.box
-    out = np.empty(info.n_stored, np.complex128)
-    step = 8192
-    for s in range(0, org.shape[0], step):
-        o = org[s:s + step]
-        x = b.x0 + (o[:, 0:1] + l % bx).ravel() * b.hx
-        y = b.y0 + (o[:, 1:2] + (l // bx) % by).ravel() * b.hy
-        z = b.z0 + (o[:, 2:3] + l // (bx * by)).ravel() * b.hz
-        out[s * bx * by * bz:(s + o.shape[0]) * bx * by * bz] = inputs.shell_initial_psi(wl, x, y, z)
-    bits = gpe.gpe_grid_mask(grid)
-    active = np.unpackbits(bits.view(np.uint8), bitorder="little").astype(bool)
-    out[~active] = 0
+    out = np.zeros(info.n_packed, np.complex128)
+    step = 1 << 22
+    for s in range(0, idx.size, step):
+        sl = slice(s, s + step)
+        out[idx[sl]] = inputs.shell_initial_psi(wl, b.x0 + i[sl] * b.hx, b.y0 + j[sl] * b.hy, b.z0 + k[sl] * b.hz)
     out *= math.sqrt(wl.N / (np.sum(np.abs(out) ** 2) * b.dV))
     return out
 
@@ -242,15 +235,16 @@ def run_ours(args):
     barrier(world)
     gpe.load()
     wl = shell_workload()
-    grid = build_grid(gpe, wl)
+    grid = build_grid(gpe, wl, tuple(args.brick), args.sched, args.chunk)
     info = gpe.gpe_grid_get_info(grid)
-    n_active, n_stored = info.n_active, info.n_stored
+    n_active, n_stored = info.n_active, info.n_packed
     psi0 = initial_compact(gpe, inputs, wl, grid)
     dt = wl.stable_dt()
     params = gpe.real_params(wl.g, dt)
 
-    st64 = gpe.gpe_state_create(grid, gpe.GPE_C64)
-    psi64 = np.ascontiguousarray(psi0.astype(np.complex64))
+    quick128 = args.quick and args.dtype == "c128"
+    st64 = gpe.gpe_state_create(grid, gpe.GPE_C128 if quick128 else gpe.GPE_C64)
+    psi64 = np.ascontiguousarray(psi0 if quick128 else psi0.astype(np.complex64))
     gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
 
     # ---- device-resident timing (complex64, the headline)
@@ -278,7 +272,7 @@ def run_ours(args):
         gpe.gpe_state_destroy(st64)
         gpe.gpe_grid_destroy(grid)
         if rank == 0:
-            print(json.dumps({"quick": True, "workload": _workload_name, "value": value,
+            print(json.dumps({"quick": True, "workload": _workload_name, "dtype": args.dtype, "value": value,
                               "ms_per_rk4_step": rk_ms, "achieved_gbs": achieved, "n_active": n_active,
                               "gpu_launches": gpu_launches}), flush=True)
         return
@@ -329,13 +323,15 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "anisotropic thin ellipsoidal shell, 1024^3 box, semi-axes 490/441/392 cells, "
                                "g=2000, N=1, mask V<5mu0, RK4 real time, complex64 bulk + FP64 reductions",
-                   "n_active": n_active, "n_stored": n_stored, "brick": f"{info.bx}x{info.by}x{info.bz}",
+                   "n_active": n_active, "n_packed": n_stored, "brick": f"{info.bx}x{info.by}x{info.bz}",
+                   "schedule": "staged" if args.sched == 0 else "wavefront",
                    "rk4_steps_per_bench_step": STEPS_PER_BENCH, "dt": dt,
                    "l2": "inputs larger than L2 (state %.0f MB + potential %.0f MB)" % (n_stored * 8 / 1e6, n_stored * 4 / 1e6),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "RK4 step (k_rk4 stage kernels)", "peak_kind": peak_kind,
+                     "kernel": "RK4 step (k_rk4_staged, four launches per step)" if args.sched == 0
+                     else "RK4 step (k_rk4_wave, one launch per step)", "peak_kind": peak_kind,
                      "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms},
         "fp64": {"value": fp64_value, "unit": "cell-steps/s", "ms_per_rk4_step": rk128_ms,
                  "fp32_over_fp64": value / fp64_value,
@@ -397,6 +393,10 @@ def main():
                     help="shell512 is the smaller case used for ncu captures")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident complex64 timing only (for profiling runs)")
+    ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront")
+    ap.add_argument("--chunk", type=int, default=0, help="bricks per wavefront task (0: default)")
+    ap.add_argument("--brick", type=int, nargs=3, default=[8, 8, 8])
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64", help="state type of a --quick run")
     args = ap.parse_args()
     global _workload_name
     _workload_name = args.workload

@@ -30,9 +30,12 @@
  *    complex128 = two float64.
  *  - Dense box arrays are laid out x fastest: cell (i, j, k) at linear index
  *    i + nx*(j + ny*k); cell centres at (x0 + i*hx, y0 + j*hy, z0 + k*hz).
- *  - The compact ("stored") layout is the library's device layout: bricks of
- *    bx*by*bz cells, brick b at offset b*bx*by*bz, cells inside a brick x
- *    fastest.  Stored cells that are not active hold zero.
+ *  - The compact layout is the library's device layout: bricks of bx*by*bz
+ *    lattice cells in brick-list order; a brick is cut into segments of 4
+ *    cells along x (local cell l = x + bx*(y + by*z), segment l/4) and stores,
+ *    in segment order, exactly the segments that hold an active cell, 4
+ *    entries each.  Cells of stored segments that are not active hold zero.
+ *    Length n_packed = 4 * (number of stored segments).
  */
 #ifndef GPE_H
 #define GPE_H
@@ -86,15 +89,25 @@ typedef struct gpe_box {
 enum { GPE_MASK_CELL = 0,   /* active = cells with V < V_cut (Sec. II A) */
        GPE_MASK_BRICK = 1 }; /* active = every in-box cell of a brick holding
                                 at least one cell with V < V_cut (Sec. II B) */
-enum { GPE_ORDER_MORTON = 0, GPE_ORDER_ZMAJOR = 1 };
+enum { GPE_ORDER_ZMAJOR = 0, GPE_ORDER_MORTON = 1 };
+
+/* Step schedules: STAGED (default) launches one kernel per stage, the
+ * paper's scheme (Sec. II B); WAVE runs every stage of a time step in one
+ * persistent launch, ordering (stage, chunk) tasks so that a stage of a chunk
+ * starts once the previous stage has finished on every chunk its stencil
+ * touches, which keeps the intermediate stage states in L2. */
+enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1 };
 
 /* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
- * all three are 0), 8x8x4, 8x4x4, 4x4x4. */
+ * all three are 0), 8x8x4, 8x4x4.  chunk = bricks per wavefront task
+ * (0: about 2048 lattice cells). */
 typedef struct gpe_grid_opts {
     int32_t bx, by, bz;
     int32_t mask_mode; /* GPE_MASK_* */
     int32_t order;     /* GPE_ORDER_* : order of the brick list in memory */
-    int32_t reserved[3];
+    int32_t sched;     /* GPE_SCHED_* */
+    int32_t chunk;
+    int32_t reserved;
 } gpe_grid_opts;
 
 enum { GPE_F64 = 1, GPE_F32 = 2 };   /* element type of a real input array */
@@ -130,6 +143,10 @@ int gpe_grid_create_analytic(const gpe_box *box, const gpe_potential *pot,
                              double V_cut, const gpe_grid_opts *opts,
                              gpe_grid **out, gpe_stream stream);
 
+/* Default brick order is z-major (bricks sorted by z, then y, then x); it
+ * bounds how far apart neighbouring bricks are in memory, which the wavefront
+ * schedule needs.  Morton order is offered for the staged schedule. */
+
 /* Grid for a potential ramp V(t) = (1 - s) V0 + s V1 (Sec. V: linear
  * interpolation between precomputed potentials).  With the cutoff blended the
  * same way, the union over s in [0, 1] of {V(s) < cut(s)} is exactly
@@ -148,7 +165,8 @@ int gpe_grid_set_potential(gpe_grid *grid, int slot, const void *V,
 typedef struct gpe_grid_info {
     int64_t n_active;  /* cells in the region of interest */
     int64_t n_bricks;
-    int64_t n_stored;  /* n_bricks * bx*by*bz */
+    int64_t n_stored;  /* lattice cells of the bricks: n_bricks * bx*by*bz */
+    int64_t n_packed;  /* length of the compact layout (active cells + padding) */
     int32_t bx, by, bz, mask_mode;
     int32_t order, n_slots; /* number of potential slots filled (1 or 2) */
     double v_max;      /* max of |V| over active cells, all slots */
@@ -160,7 +178,9 @@ int gpe_grid_get_info(const gpe_grid *grid, gpe_grid_info *out);
 /* Host copies of the layout: brick origins in cells (3 int32 per brick,
  * i0 j0 k0), the neighbour table (6 int32 per brick: -x +x -y +y -z +z, -1 =
  * absent; may be NULL), the active-cell bit mask (n_stored/32 words, bit l of
- * word w = stored cell 32w + l), and potential slot `slot` (n_stored doubles).
+ * word w = lattice cell 32w + l of the brick list), and potential slot `slot`
+ * in the compact layout (n_packed doubles; slot 0 holds +inf at the inactive
+ * cells of stored segments, which is how the kernels tell them apart).
  * Synchronous. */
 int gpe_grid_bricks(const gpe_grid *grid, int32_t *origins, int32_t *nbr);
 int gpe_grid_mask(const gpe_grid *grid, uint32_t *bits);

@@ -56,7 +56,6 @@ int shape_id(int bx, int by, int bz)
     if (bx == 8 && by == 8 && bz == 8) return 0;
     if (bx == 8 && by == 8 && bz == 4) return 1;
     if (bx == 8 && by == 4 && bz == 4) return 2;
-    if (bx == 4 && by == 4 && bz == 4) return 3;
     return -1;
 }
 

@@ -1,15 +1,21 @@
 // gpe_internal.cuh -- shared internals of libgpeshell (not part of the ABI).
 //
-// Layout of a grid in device memory (all arrays indexed by "slot" =
-// brick * BC + local, local = x + BX*(y + BY*z) inside the brick):
-//   d_org  [nb*3]  int32   brick origin in cells (i0, j0, k0)
-//   d_nbr  [nb*6]  int32   face-neighbour brick ids (-x +x -y +y -z +z), -1 = none
-//   d_mask [ns/32] uint32  active-cell bits, bit (slot & 31) of word slot/32
-//   d_V[s] [ns]    double  potential slot s (0: V or V0, 1: V1)
-// Inactive slots of every wavefunction-like array hold exactly zero and are
-// never written by the step kernels, so a neighbour read of an inactive or
-// absent cell yields psi = 0 (Dirichlet zero on the deleted rows/columns of
-// the Laplacian, Sec. II A).
+// Layout of a grid in device memory.  Bricks of BC = BX*BY*BZ lattice cells,
+// local index l = x + BX*(y + BY*z); "slot" = brick * BC + l addresses the
+// lattice.  A segment is 4 consecutive cells along x (local segment q = l/4).
+// Only segments holding an active cell are stored ("packed" layout):
+//   d_org  [nb*3]  int32    brick origin in cells (i0, j0, k0)
+//   d_nbr  [nb*6]  int32    face-neighbour brick ids (-x +x -y +y -z +z), -1 = none
+//   d_mask [ns/32] uint32   active-cell bits of the lattice, bit slot&31 of word slot/32
+//   d_rec  [nb]    BrickRec stored-segment bits, per-word prefix counts, packed offset
+//   d_V[s] [n_packed] double potential slot s (0: V or V0, 1: V1); the inactive
+//                           cells of stored segments hold +inf in slot 0
+// Packed index of cell l of brick b (if its segment is stored):
+//   rec.off + 4*(rank of segment l/4 among the brick's stored segments) + l%4.
+// Inactive cells of stored segments hold psi = 0 and are never updated (the
+// +inf potential marks them); cells of absent segments and bricks are not
+// stored and read as psi = 0: Dirichlet zero on the rows/columns deleted
+// from the Laplacian (Sec. II A).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -56,9 +62,32 @@ void dev_free(void *p);
 inline cudaStream_t S(gpe_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // supported brick shapes; the kernels are instantiated for each
-int shape_id(int bx, int by, int bz);  // 0: 8x8x8, 1: 8x8x4, 2: 8x4x4, 3: 4x4x4
+int shape_id(int bx, int by, int bz);  // 0: 8x8x8, 1: 8x8x4, 2: 8x4x4
 
 int sm_count(int device);
+
+// per-brick record of the packed layout (32 bytes)
+struct BrickRec {
+    uint32_t m[4];  // bit q: segment q is stored
+    uint32_t off;   // packed index of the brick's first stored cell
+    uint32_t pre;   // byte w: stored segments in mask words < w
+    uint32_t pad[2];
+};
+
+// packed index of the first cell of segment q, if stored
+__host__ __device__ __forceinline__ bool seg_index(const BrickRec &r, int q, uint32_t &idx)
+{
+    const int w = q >> 5, bit = q & 31;
+    const uint32_t m = r.m[w];
+    if (!((m >> bit) & 1u)) return false;
+#ifdef __CUDA_ARCH__
+    const uint32_t below = __popc(m & ((1u << bit) - 1u));
+#else
+    const uint32_t below = (uint32_t)__builtin_popcount(m & ((1u << bit) - 1u));
+#endif
+    idx = r.off + 4u * (((r.pre >> (8 * w)) & 0xffu) + below);
+    return true;
+}
 
 // ------------------------------------------------------------ complex types
 template <typename R> struct Cx;
@@ -254,12 +283,22 @@ struct gpe_grid {
     int mask_mode = 0, order = 0;
     int64_t nbx = 0, nby = 0, nbz = 0;
     int64_t nb = 0, n_stored = 0, n_active = 0;
+    int64_t n_packed = 0;
     int32_t *d_org = nullptr;
     int32_t *d_nbr = nullptr;
     uint32_t *d_mask = nullptr;
+    gpe::BrickRec *d_rec = nullptr;
     int32_t *d_bvol = nullptr;  // brick-grid volume nbx*nby*nbz -> brick id or -1
     double *d_V[2] = {nullptr, nullptr};
     float *d_Vf[2] = {nullptr, nullptr};  // float copies, made on first use
+    // wavefront schedule (built on first use): chunks of `cb` consecutive
+    // bricks, the chunk range each chunk's stencils touch, and the task order
+    // for 2-stage (imaginary time) and 4-stage (RK4) steps
+    int cb = 0;
+    int64_t n_chunks = 0;
+    int32_t *d_chunk_lohi = nullptr;  // [n_chunks*2]
+    int32_t *d_tasks = nullptr;       // [2*n_chunks] for 2 stages, then [4*n_chunks] for 4
+    int sched = -1;                   // GPE_SCHED_* used by the step calls
     int n_slots = 1;
     double v_max = 0.0;
     int nsm = 0;
@@ -270,13 +309,20 @@ struct gpe_state {
     gpe_grid *grid = nullptr;
     int dtype = GPE_C128;
     size_t elem = 16;       // bytes per complex element
-    void *d_psi = nullptr;  // n_stored complex
+    void *d_psi = nullptr;  // n_packed complex
     void *d_work[3] = {nullptr, nullptr, nullptr};  // RK4 y2,y3,y4 / ITP tmp
     void *d_E = nullptr;    // ITP exp(-V dt/2), state precision
     double E_dt = -1.0;     // dt that d_E was made for
     double *d_clock = nullptr;  // device time base for ramps
     gpe::RedScratch red;
     gpe_obs *h_obs = nullptr;   // pinned host landing buffer
+    // wavefront bookkeeping: per-chunk completion stamps (monotonic), the
+    // dynamic ticket counter, the finish counter and a device error word
+    uint32_t *d_done = nullptr;
+    unsigned long long *d_ctr = nullptr;  // [0] tickets, [1] finished ITP chunks, [2] error
+    double *d_chunk_norm = nullptr;       // per-chunk FP64 partial norms (ITP)
+    uint32_t epoch = 0;                   // stages completed so far (flags compare to it)
+    unsigned long long ticket_base = 0, finish_base = 0;
 };
 
 namespace gpe {

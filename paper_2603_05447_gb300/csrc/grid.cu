@@ -256,34 +256,74 @@ __global__ void k_cells(VSource src, BoxD box, int BX, int BY, int BZ, int mask_
     }
 }
 
-// replace a potential slot from a dense array (region unchanged)
-__global__ void k_set_potential(const void *dense, int dtype, BoxD box, int BX, int BY, int BZ,
-                                const int32_t *org, double *V)
+// Segment layout: a segment is 4 consecutive cells along x inside a brick
+// (one 32-byte sector of complex64).  A brick stores exactly its segments that
+// hold at least one active cell.  k_seg_records builds each brick's record:
+// the segment bit mask, the number of stored segments before each mask word,
+// and (after the host scan) the packed offset.
+__global__ void k_seg_records(int64_t nb, int BC, const uint32_t *mask, BrickRec *rec, uint32_t *cnt)
 {
-    const int64_t id = blockIdx.x;
-    const int BC = BX * BY * BZ;
-    for (int l = threadIdx.x; l < BC; l += blockDim.x) {
-        int64_t i = org[3 * id] + l % BX, j = org[3 * id + 1] + (l / BX) % BY,
-                k = org[3 * id + 2] + l / (BX * BY);
-        double v = 0.0;
-        if (i < box.nx && j < box.ny && k < box.nz) {
-            int64_t lin = i + box.nx * (j + box.ny * k);
-            v = dtype == GPE_F64 ? ((const double *)dense)[lin] : (double)((const float *)dense)[lin];
-        }
-        V[id * BC + l] = v;
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int W = BC / 32, nseg = BC / 4;
+    BrickRec r{};
+    uint32_t c = 0;
+    for (int q = 0; q < nseg; ++q) {
+        // cells 4q..4q+3 of the brick: nibble (q & 7) of mask word q/8
+        const uint32_t word = mask[b * W + (q >> 3)];
+        if ((word >> (4 * (q & 7))) & 0xfu) r.m[q >> 5] |= 1u << (q & 31);
+    }
+    for (int w = 0; w < 4; ++w) {
+        r.pre |= (c & 0xffu) << (8 * w);
+        c += __popc(r.m[w]);
+    }
+    rec[b] = r;
+    cnt[b] = c;
+}
+
+// scatter stored-lattice values to the packed layout: active cells get their
+// value, inactive cells of stored segments get `fill`
+__global__ void k_pack(int64_t ns, int BC, const uint32_t *mask, const BrickRec *rec, const double *src,
+                       double *dst, double fill)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = s / BC;
+        const int l = (int)(s % BC);
+        uint32_t idx;
+        if (!seg_index(rec[b], l >> 2, idx)) continue;
+        const bool act = (mask[s >> 5] >> (s & 31)) & 1u;
+        dst[idx + (l & 3)] = act ? src[s] : fill;
     }
 }
 
-__global__ void k_vmax(int64_t ns, const uint32_t *mask, const double *V0, const double *V1,
-                       unsigned long long *vmax_bits)
+// replace a potential slot from a dense array (region unchanged)
+__global__ void k_set_potential(const void *dense, int dtype, BoxD box, int BX, int BY, int BZ,
+                                const int32_t *org, const uint32_t *mask, const BrickRec *rec, double *V)
+{
+    const int64_t id = blockIdx.x;
+    const int BC = BX * BY * BZ, W = BC / 32;
+    for (int l = threadIdx.x; l < BC; l += blockDim.x) {
+        const uint32_t word = mask[id * W + (l >> 5)];
+        if (!((word >> (l & 31)) & 1u)) continue;   // active cells are always inside the box
+        uint32_t idx;
+        if (!seg_index(rec[id], l >> 2, idx)) continue;
+        int64_t i = org[3 * id] + l % BX, j = org[3 * id + 1] + (l / BX) % BY,
+                k = org[3 * id + 2] + l / (BX * BY);
+        int64_t lin = i + box.nx * (j + box.ny * k);
+        V[idx + (l & 3)] = dtype == GPE_F64 ? ((const double *)dense)[lin] : (double)((const float *)dense)[lin];
+    }
+}
+
+// max |V| over the active cells of the packed arrays (inactive cells of
+// stored segments hold +inf in V0 and are skipped)
+__global__ void k_vmax(int64_t np, const double *V0, const double *V1, unsigned long long *vmax_bits)
 {
     double vm = 0.0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < np;
          s += (int64_t)gridDim.x * blockDim.x) {
-        if ((mask[s >> 5] >> (s & 31)) & 1u) {
-            vm = fmax(vm, fabs(V0[s]));
-            if (V1) vm = fmax(vm, fabs(V1[s]));
-        }
+        if (!(V0[s] < INFINITY)) continue;
+        vm = fmax(vm, fabs(V0[s]));
+        if (V1) vm = fmax(vm, fabs(V1[s]));
     }
     for (int off = 16; off > 0; off >>= 1) vm = fmax(vm, __shfl_down_sync(0xffffffffu, vm, off));
     if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(vm));
@@ -328,6 +368,9 @@ static PotDesc potdesc(const gpe_potential &p)
 static void grid_free(gpe_grid *g)
 {
     if (!g) return;
+    dev_free(g->d_rec);
+    dev_free(g->d_chunk_lohi);
+    dev_free(g->d_tasks);
     dev_free(g->d_org);
     dev_free(g->d_nbr);
     dev_free(g->d_mask);
@@ -348,12 +391,15 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     if (o.bx == 0 && o.by == 0 && o.bz == 0) o.bx = o.by = o.bz = 8;
     const int shape = shape_id(o.bx, o.by, o.bz);
     if (shape < 0)
-        return fail(GPE_ERR_ARG, "unsupported brick shape %dx%dx%d (use 8x8x8, 8x8x4, 8x4x4, 4x4x4)",
-                    o.bx, o.by, o.bz);
+        return fail(GPE_ERR_ARG, "unsupported brick shape %dx%dx%d (use 8x8x8, 8x8x4 or 8x4x4)", o.bx, o.by,
+                    o.bz);
     if (o.mask_mode != GPE_MASK_CELL && o.mask_mode != GPE_MASK_BRICK)
         return fail(GPE_ERR_ARG, "unknown mask mode %d", o.mask_mode);
     if (o.order != GPE_ORDER_MORTON && o.order != GPE_ORDER_ZMAJOR)
         return fail(GPE_ERR_ARG, "unknown brick order %d", o.order);
+    if (o.sched != GPE_SCHED_WAVE && o.sched != GPE_SCHED_STAGED)
+        return fail(GPE_ERR_ARG, "unknown schedule %d", o.sched);
+    if (o.chunk < 0 || o.chunk > 4096) return fail(GPE_ERR_ARG, "chunk must be in [0, 4096]");
 
     gpe_grid *g = new gpe_grid();
     GPE_TRY_CUDA(cudaGetDevice(&g->device));
@@ -366,6 +412,8 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     g->shape = shape;
     g->mask_mode = o.mask_mode;
     g->order = o.order;
+    g->sched = o.sched;
+    g->cb = o.chunk > 0 ? o.chunk : std::max(1, 2048 / g->bc);
     g->nbx = (box->nx + o.bx - 1) / o.bx;
     g->nby = (box->ny + o.by - 1) / o.by;
     g->nbz = (box->nz + o.bz - 1) / o.bz;
@@ -376,12 +424,23 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     int64_t *bsum = nullptr;
     int32_t *coords = nullptr;
     unsigned long long *counters = nullptr;
+    double *tmpV[2] = {nullptr, nullptr};
+    uint32_t *cnt = nullptr;
     int rc = GPE_OK;
     auto cleanup = [&]() {
         dev_free(occ);
         dev_free(bsum);
         dev_free(coords);
         dev_free(counters);
+        dev_free(tmpV[0]);
+        dev_free(tmpV[1]);
+        dev_free(cnt);
+        occ = nullptr;
+        bsum = nullptr;
+        coords = nullptr;
+        counters = nullptr;
+        tmpV[0] = tmpV[1] = nullptr;
+        cnt = nullptr;
     };
 #define BUILD_TRY(x)                 \
     do {                             \
@@ -459,16 +518,16 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     BUILD_CUDA(cudaGetLastError());
 
     BUILD_TRY(dev_alloc_t(&g->d_mask, g->n_stored / 32));
-    BUILD_TRY(dev_alloc_t(&g->d_V[0], g->n_stored));
+    BUILD_TRY(dev_alloc_t(&tmpV[0], g->n_stored));
     if (src.mode == 2) {
-        BUILD_TRY(dev_alloc_t(&g->d_V[1], g->n_stored));
+        BUILD_TRY(dev_alloc_t(&tmpV[1], g->n_stored));
         g->n_slots = 2;
     }
     BUILD_TRY(dev_alloc_t(&counters, 2));
     BUILD_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     if (total > 0x7fffffffLL) BUILD_TRY(fail(GPE_ERR_ARG, "too many bricks"));
     k_cells<<<(unsigned)total, std::min(g->bc, 256), 0, st>>>(src, bd, o.bx, o.by, o.bz, o.mask_mode,
-                                                            g->d_org, g->d_V[0], g->d_V[1], g->d_mask,
+                                                            g->d_org, tmpV[0], tmpV[1], g->d_mask,
                                                             counters, counters + 1);
     BUILD_CUDA(cudaGetLastError());
     unsigned long long hc[2];
@@ -477,6 +536,33 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     g->n_active = (int64_t)hc[0];
     long long vb = (long long)hc[1];
     memcpy(&g->v_max, &vb, sizeof(double));
+
+    // packed layout: every brick stores its segments (4 cells along x) that
+    // hold an active cell, in lattice order, as one run
+    BUILD_TRY(dev_alloc_t(&g->d_rec, total));
+    BUILD_TRY(dev_alloc_t(&cnt, total));
+    k_seg_records<<<nbb, 256, 0, st>>>(total, g->bc, g->d_mask, g->d_rec, cnt);
+    BUILD_CUDA(cudaGetLastError());
+    std::vector<uint32_t> hcnt(total);
+    std::vector<BrickRec> hrec(total);
+    BUILD_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaMemcpyAsync(hrec.data(), g->d_rec, total * sizeof(BrickRec), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaStreamSynchronize(st));
+    uint64_t acc = 0;
+    for (int64_t b = 0; b < total; ++b) {
+        hrec[b].off = (uint32_t)acc;
+        acc += 4ull * hcnt[b];
+        if (acc >= 0xffffffffull) BUILD_TRY(fail(GPE_ERR_ARG, "too many stored cells for 32-bit offsets"));
+    }
+    g->n_packed = (int64_t)acc;
+    BUILD_CUDA(cudaMemcpyAsync(g->d_rec, hrec.data(), total * sizeof(BrickRec), cudaMemcpyHostToDevice, st));
+    for (int sl = 0; sl < g->n_slots; ++sl) {
+        BUILD_TRY(dev_alloc_t(&g->d_V[sl], g->n_packed));
+        k_pack<<<g->nsm * 8, 256, 0, st>>>(g->n_stored, g->bc, g->d_mask, g->d_rec, tmpV[sl], g->d_V[sl],
+                                          sl == 0 ? (double)INFINITY : 0.0);
+        BUILD_CUDA(cudaGetLastError());
+    }
+    BUILD_CUDA(cudaStreamSynchronize(st));
     cleanup();
 #undef BUILD_TRY
 #undef BUILD_CUDA
@@ -509,11 +595,11 @@ static int stage_dense(const gpe_box *box, const void *V, int V_dtype, int on_de
 int ensure_vf(gpe_grid *g, int slot)
 {
     if (g->d_Vf[slot]) return GPE_OK;
-    GPE_TRY(dev_alloc_t(&g->d_Vf[slot], g->n_stored));
+    GPE_TRY(dev_alloc_t(&g->d_Vf[slot], g->n_packed));
     // conversion is ordered on the legacy stream; synchronise so that any
     // stream sees the finished copy
     extern int convert_to_float(const double *src, float *dst, int64_t n);
-    GPE_TRY(convert_to_float(g->d_V[slot], g->d_Vf[slot], g->n_stored));
+    GPE_TRY(convert_to_float(g->d_V[slot], g->d_Vf[slot], g->n_packed));
     return GPE_OK;
 }
 
@@ -587,10 +673,15 @@ extern "C" int gpe_grid_set_potential(gpe_grid *g, int slot, const void *V, int 
     void *owned = nullptr;
     GPE_TRY(stage_dense(&g->box, V, V_dtype, V_on_device, &dptr, &owned, st));
     int rc = GPE_OK;
-    if (!g->d_V[slot]) rc = dev_alloc_t(&g->d_V[slot], g->n_stored);
+    if (!g->d_V[slot]) {
+        rc = dev_alloc_t(&g->d_V[slot], g->n_packed);
+        if (rc == GPE_OK && cudaMemset(g->d_V[slot], 0, g->n_packed * sizeof(double)) != cudaSuccess)
+            rc = fail(GPE_ERR_CUDA, "cudaMemset(V) failed");
+    }
     if (rc == GPE_OK) {
         k_set_potential<<<(unsigned)g->nb, std::min(g->bc, 256), 0, st>>>(dptr, V_dtype, boxd(g->box), g->bx,
-                                                                        g->by, g->bz, g->d_org, g->d_V[slot]);
+                                                                        g->by, g->bz, g->d_org, g->d_mask,
+                                                                        g->d_rec, g->d_V[slot]);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "k_set_potential", __FILE__, __LINE__);
     }
@@ -599,7 +690,7 @@ extern "C" int gpe_grid_set_potential(gpe_grid *g, int slot, const void *V, int 
     if (rc == GPE_OK) rc = dev_alloc_t(&vb, 1);
     if (rc == GPE_OK) {
         cudaMemsetAsync(vb, 0, sizeof(unsigned long long), st);
-        k_vmax<<<g->nsm * 4, 256, 0, st>>>(g->n_stored, g->d_mask, g->d_V[0], g->n_slots > 1 ? g->d_V[1] : nullptr, vb);
+        k_vmax<<<g->nsm * 4, 256, 0, st>>>(g->n_packed, g->d_V[0], g->n_slots > 1 ? g->d_V[1] : nullptr, vb);
         unsigned long long h = 0;
         cudaMemcpyAsync(&h, vb, sizeof h, cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
@@ -625,6 +716,7 @@ extern "C" int gpe_grid_get_info(const gpe_grid *g, gpe_grid_info *out)
     out->n_active = g->n_active;
     out->n_bricks = g->nb;
     out->n_stored = g->n_stored;
+    out->n_packed = g->n_packed;
     out->bx = g->bx;
     out->by = g->by;
     out->bz = g->bz;
@@ -655,7 +747,7 @@ extern "C" int gpe_grid_potential(const gpe_grid *g, int slot, double *V)
 {
     if (!g || !V) return fail(GPE_ERR_ARG, "NULL argument");
     if (slot < 0 || slot > 1 || !g->d_V[slot]) return fail(GPE_ERR_ARG, "potential slot %d not set", slot);
-    GPE_TRY_CUDA(cudaMemcpy(V, g->d_V[slot], g->n_stored * sizeof(double), cudaMemcpyDeviceToHost));
+    GPE_TRY_CUDA(cudaMemcpy(V, g->d_V[slot], g->n_packed * sizeof(double), cudaMemcpyDeviceToHost));
     return GPE_OK;
 }
 

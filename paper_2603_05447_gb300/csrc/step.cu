@@ -3,14 +3,30 @@
 //
 // Every stencil kernel stages one brick plus its face halo in shared memory
 // (the paper's per-block tile of Sec. II B, gathered here from the six face
-// neighbours through the brick-neighbour table), evaluates the 7-point
-// Laplacian of Eq. (B1) from the tile, applies the pointwise terms of the
-// equation and writes only active cells.  Blocks walk the brick list with a
-// fixed stride (block b handles bricks b, b + gridDim, ...), so per-block
-// partial sums, and therefore every FP64 reduction, are deterministic.
+// neighbours through the brick-neighbour table and the packed-layout ranks),
+// evaluates the 7-point Laplacian of Eq. (B1) from the tile, applies the
+// pointwise terms of the equation and writes the active cells.
+//
+// Two schedules run the same per-brick arithmetic:
+//  * STAGED: one launch per stage; blocks walk the brick list with a fixed
+//    stride, so per-block partial sums (and every FP64 reduction) are
+//    deterministic.
+//  * WAVE: one persistent launch per time step.  The work is split into
+//    (stage, chunk) tasks, a chunk being `cb` consecutive bricks.  Tasks are
+//    handed out from an atomic ticket counter in an order where every
+//    dependency of a task has a smaller ticket (stage s of chunk c needs stage
+//    s-1 of every chunk its stencils read), and a task waits for those
+//    completion stamps before it reads.  The live window of intermediate
+//    stage states is a few brick layers wide, so it stays in L2 instead of
+//    making a round trip through HBM per stage.  Waits are bounded (about 2 s);
+//    a wait that runs out sets the state's error word and the call that reads
+//    results reports GPE_ERR_CUDA.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "gpe_internal.cuh"
 
@@ -32,15 +48,15 @@ int convert_to_float(const double *src, float *dst, int64_t n)
 }
 
 __global__ void k_set_scalar(double *p, double v) { *p = v; }
-__global__ void k_add_scalar(double *p, double v) { *p += v; }
 
 // E = exp(-V dt/2) in the state precision (Eq. (7): the diagonal propagator
-// is precomputed once per dt)
+// is precomputed once per dt); E = -1 marks the inactive cells of stored
+// segments (V = +inf there)
 template <typename R>
 __global__ void k_make_E(const double *V, R *E, int64_t n, double dt)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        E[i] = (R)exp(-V[i] * dt / 2.0);
+        E[i] = V[i] < INFINITY ? (R)exp(-V[i] * dt / 2.0) : (R)-1;
 }
 
 // ------------------------------------------------------------ launch helper
@@ -48,40 +64,251 @@ static std::mutex g_occ_mu;
 static std::unordered_map<const void *, int> g_occ;
 
 template <typename K>
-static int blocks_for(K kernel, const gpe_grid *g, int threads)
+static int per_sm_for(K kernel, int threads)
 {
-    int per_sm = 0;
     {
         std::lock_guard<std::mutex> lk(g_occ_mu);
         auto it = g_occ.find((const void *)kernel);
-        if (it != g_occ.end()) per_sm = it->second;
+        if (it != g_occ.end()) return it->second;
     }
-    if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        std::lock_guard<std::mutex> lk(g_occ_mu);
-        g_occ[(const void *)kernel] = per_sm;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
     }
-    int64_t b = (int64_t)g->nsm * per_sm;
-    if (b > g->nb) b = g->nb;
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    g_occ[(const void *)kernel] = per_sm;
+    return per_sm;
+}
+
+// every brick kernel runs blocks of 256 threads, one brick per warp
+template <typename K>
+static int blocks_for(K kernel, const gpe_grid *g, int threads)
+{
+    int64_t b = (int64_t)g->nsm * per_sm_for(kernel, threads);
+    const int64_t need = (g->nb + 7) / 8;
+    if (b > need) b = need;
     if (b < 1) b = 1;
     return (int)b;
 }
 
-static inline int brick_threads(const gpe_grid *g) { return g->bc < 256 ? g->bc : 256; }
+static inline int brick_threads(const gpe_grid *) { return 256; }
 
 #define GPE_SHAPES(M) \
     M(0, 8, 8, 8)     \
     M(1, 8, 8, 4)     \
-    M(2, 8, 4, 4)     \
-    M(3, 4, 4, 4)
+    M(2, 8, 4, 4)
+
+// ------------------------------------------------------------ packed layout
+struct GridView {
+    const int32_t *nbr;
+    const BrickRec *rec;
+    int64_t nb;
+};
+
+static GridView view(const gpe_grid *g) { return GridView{g->d_nbr, g->d_rec, g->nb}; }
+
+// segment geometry of a brick shape (BX must be 8: two segments per row)
+template <int BX, int BY, int BZ>
+struct Seg {
+    static_assert(BX == 8, "bricks are 8 cells long in x");
+    static constexpr int SX = BX / 4;          // segments per x-row
+    static constexpr int PLANE = SX * BY;      // segments per z-plane (divides 32)
+    static constexpr int NSEG = PLANE * BZ;    // segments per brick
+    static constexpr int NIT = NSEG / 32;      // warp iterations per brick
+    static_assert(32 % PLANE == 0 && NSEG % 32 == 0, "brick shape must tile the warp");
+};
+
+template <typename CT>
+__device__ __forceinline__ CT czero()
+{
+    CT z;
+    z.x = 0;
+    z.y = 0;
+    return z;
+}
+
+__device__ __forceinline__ float2 shfl_up(float2 v, int d)
+{
+    v.x = __shfl_up_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_up_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ double2 shfl_up(double2 v, int d)
+{
+    v.x = __shfl_up_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_up_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ float2 shfl_down(float2 v, int d)
+{
+    v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ double2 shfl_down(double2 v, int d)
+{
+    v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ float2 shfl_xor(float2 v, int d)
+{
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ double2 shfl_xor(double2 v, int d)
+{
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, d);
+    return v;
+}
+
+// 4 consecutive complex values (one segment); CG: read through L2 only
+// (data written by other blocks of the same launch)
+template <bool CG>
+__device__ __forceinline__ void ld4(const float2 *p, float2 (&v)[4])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float4 a = CG ? __ldcg(q) : q[0], b = CG ? __ldcg(q + 1) : q[1];
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+template <bool CG>
+__device__ __forceinline__ void ld4(const double2 *p, double2 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = CG ? __ldcg(p + i) : p[i];
+}
+__device__ __forceinline__ void st4(float2 *p, const float2 (&v)[4])
+{
+    float4 *q = reinterpret_cast<float4 *>(p);
+    q[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    q[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+__device__ __forceinline__ void st4(double2 *p, const double2 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = v[i];
+}
+__device__ __forceinline__ void ldr4(const float *p, float (&v)[4])
+{
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+__device__ __forceinline__ void ldr4(const double *p, double (&v)[4])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+struct Identity {
+    template <typename CT>
+    __device__ __forceinline__ CT operator()(CT v, uint32_t) const { return v; }
+};
+
+// Records of brick b (slot 0) and of its six face neighbours (slots 1..6,
+// order -x +x -y +y -z +z; an absent neighbour gets an empty record), loaded by
+// one warp into its shared-memory slots.
+__device__ __forceinline__ void load_recs(BrickRec *R, const GridView &G, int64_t b)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (lane < 7) {
+        const int64_t id = lane == 0 ? b : (int64_t)__ldg(&G.nbr[b * 6 + lane - 1]);
+        uint4 a = make_uint4(0, 0, 0, 0), c = make_uint4(0, 0, 0, 0);
+        if (id >= 0) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(G.rec + id);
+            a = __ldg(p);
+            c = __ldg(p + 1);
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(R + lane);
+        d[0] = a;
+        d[1] = c;
+    }
+    __syncwarp();
+}
+
+// One lane's segment q of a brick: its four values c[] and their 7-point
+// Laplacians L[] (Eq. (B1)), every loaded value passed through xf first.
+// All 32 lanes must call this together: x and y neighbours inside the brick
+// come from other lanes by shuffles; z neighbours and brick-boundary
+// neighbours are loaded.  Every load of the lane is issued before the first
+// shuffle so that they are in flight together.
+template <bool CG, typename CT>
+__device__ __forceinline__ CT ld1(const CT *p)
+{
+    return CG ? __ldcg(p) : *p;
+}
+
+template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF>
+__device__ __forceinline__ void gather(const CT *src, const BrickRec *Rr, int q, bool stored, uint32_t idx, XF xf,
+                                       R ihx2, R ihy2, R ihz2, CT (&c)[4], CT (&L)[4])
+{
+    using S = Seg<BX, BY, BZ>;
+    const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
+    // neighbour segments that live in memory
+    uint32_t jzm = 0, jzp = 0, jy = 0, jx = 0;
+    const bool hzm = stored && (z == 0 ? seg_index(Rr[5], q + S::PLANE * (BZ - 1), jzm)
+                                       : seg_index(Rr[0], q - S::PLANE, jzm));
+    const bool hzp = stored && (z == BZ - 1 ? seg_index(Rr[6], q - S::PLANE * (BZ - 1), jzp)
+                                            : seg_index(Rr[0], q + S::PLANE, jzp));
+    const bool ylo = (y == 0), yhi = (y == BY - 1);
+    const bool hy = stored && (ylo ? seg_index(Rr[3], hx + S::SX * (BY - 1) + S::PLANE * z, jy)
+                                   : (yhi && seg_index(Rr[4], hx + S::PLANE * z, jy)));
+    // x: segment (1, y, z) of the -x brick (cell x = 7) or (0, y, z) of the +x brick (cell x = 0)
+    const bool hxb = stored && (hx == 0 ? seg_index(Rr[1], q + 1, jx) : seg_index(Rr[2], q - 1, jx));
+    if (hx == 0) jx += 3;
+    CT zm[4], zp[4], yb[4], xb = czero<CT>();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = zm[i] = zp[i] = yb[i] = czero<CT>();
+    if (stored) ld4<CG>(src + idx, c);
+    if (hzm) ld4<CG>(src + jzm, zm);
+    if (hzp) ld4<CG>(src + jzp, zp);
+    if (hy) ld4<CG>(src + jy, yb);
+    if (hxb) xb = ld1<CG>(src + jx);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (stored) c[i] = xf(c[i], idx + i);
+        if (hzm) zm[i] = xf(zm[i], jzm + i);
+        if (hzp) zp[i] = xf(zp[i], jzp + i);
+        if (hy) yb[i] = xf(yb[i], jy + i);
+    }
+    if (hxb) xb = xf(xb, jx);
+    CT ym[4], yp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        ym[i] = shfl_up(c[i], S::SX);
+        yp[i] = shfl_down(c[i], S::SX);
+        if (ylo) ym[i] = yb[i];
+        if (yhi) yp[i] = yb[i];
+    }
+    const CT p0 = shfl_xor(c[0], 1), p3 = shfl_xor(c[3], 1);
+    const CT xm = hx == 0 ? xb : p3;  // left of cell 0
+    const CT xp = hx == 0 ? p0 : xb;  // right of cell 3
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const CT l = i == 0 ? xm : c[i - 1];
+        const CT r = i == 3 ? xp : c[i + 1];
+        L[i].x = (r.x - 2 * c[i].x + l.x) * ihx2 + (yp[i].x - 2 * c[i].x + ym[i].x) * ihy2 +
+                 (zp[i].x - 2 * c[i].x + zm[i].x) * ihz2;
+        L[i].y = (r.y - 2 * c[i].y + l.y) * ihx2 + (yp[i].y - 2 * c[i].y + ym[i].y) * ihy2 +
+                 (zp[i].y - 2 * c[i].y + zm[i].y) * ihz2;
+    }
+}
 
 // ------------------------------------------------------------ ramp schedule
 struct Ramp {
     const double *clock;  // device time base
-    double t_off;         // stage time = *clock + t_off
     double T;
     int n_knots;
     double knots[GPE_MAX_KNOTS];
@@ -100,290 +327,441 @@ __device__ __forceinline__ double ramp_s(const Ramp &r, double t)
     return (1.0 - w) * r.knots[k] + w * r.knots[k + 1];
 }
 
+// ------------------------------------------------------------ wavefront sync
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
+constexpr long long WAIT_ITERS = 40000000LL;           // backstop if the timer stalls
+
+// Called by all 32 lanes of one warp: wait until done[c] >= target for every
+// chunk c in [lo, hi].  Returns false (and sets *err) if the wait runs out.
+__device__ bool wait_chunks(const uint32_t *done, int lo, int hi, uint32_t target, unsigned long long *err)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < WAIT_ITERS; ++it) {
+        bool ok = true;
+        for (int i = lo + lane; i <= hi; i += 32) ok = ok && (ld_acquire(done + i) >= target);
+        if (__all_sync(0xffffffffu, ok)) return true;
+        if (global_ns() - t0 > WAIT_NS) break;
+        __nanosleep(200);
+    }
+    if (lane == 0) atomicOr(err, 1ull);
+    return false;
+}
+
+// Invalidate, without write-back, the L2 lines lying wholly inside
+// [p, p + bytes): the data is dead (every reader has finished).
+__device__ __forceinline__ void discard_range(const void *p, size_t bytes)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t first = (a + 127) & ~uintptr_t(127);
+    const uintptr_t last = (a + bytes) & ~uintptr_t(127);
+    for (uintptr_t q = first + (uintptr_t)threadIdx.x * 128; q + 128 <= last; q += (uintptr_t)blockDim.x * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(q) : "memory");
+}
+
+struct Wave {
+    const int32_t *tasks;      // packed (stage << 28) | chunk, in dependency-safe order
+    const int32_t *lohi;       // chunk range read by each chunk's stencils
+    uint32_t *done;            // completion stamp per chunk
+    unsigned long long *ctr;   // [0] tickets, [1] finished chunks, [2] error word
+    unsigned long long ticket_base;
+    unsigned long long finish_base;
+    uint32_t epoch;            // stamp before this launch
+    int ntasks;
+    int cb;                    // bricks per chunk
+    int nchunks;
+    uint32_t n_packed;
+};
+
+// grab the next task of this launch; -1 when none is left
+__device__ __forceinline__ int next_task(const Wave &w)
+{
+    __shared__ int s_task;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t = atomicAdd(&w.ctr[0], 1ull) - w.ticket_base;
+        s_task = t < (unsigned long long)w.ntasks ? w.tasks[t] : -1;
+    }
+    __syncthreads();
+    return s_task;
+}
+
+__device__ __forceinline__ void wait_for(const Wave &w, int st, int c)
+{
+    if (st > 0 && threadIdx.x < 32)
+        wait_chunks(w.done, w.lohi[2 * c], w.lohi[2 * c + 1], w.epoch + (uint32_t)st, &w.ctr[2]);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void publish(const Wave &w, int st, int c)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(w.done + c, w.epoch + (uint32_t)st + 1u);
+}
+
 // ------------------------------------------------------------ RK4 stages
 // Memory-optimised RK4 (App. A, RK4 a* and b*): the stage states are stored
 // instead of the k_i, so stage i reads only the state it differentiates (with
 // halo) plus the own-cell values of earlier states:
-//   ST1: y2 = y0 + dt/2 f(t, y0)
-//   ST2: y3 = y0 + dt/2 f(t + dt/2, y2)
-//   ST3: y4 = y0 + dt   f(t + dt/2, y3)
-//   ST4: y1 = (-y0 + y2 + 2 y3 + y4)/3 + dt/6 f(t + dt, y4)   (in place of y0)
+//   stage 0: y2 = y0 + dt/2 f(t, y0)
+//   stage 1: y3 = y0 + dt/2 f(t + dt/2, y2)
+//   stage 2: y4 = y0 + dt   f(t + dt/2, y3)
+//   stage 3: y1 = (-y0 + y2 + 2 y3 + y4)/3 + dt/6 f(t + dt, y4)  (in place of y0)
 // with f(t, y) = -i [ -1/2 lap y + (V(t) + g|y|^2) y ]  (Eq. (8)).
 template <typename R>
 struct RkArgs {
     using CT = typename Cx<R>::T;
-    const CT *yin;
-    const CT *y0;
-    const CT *y2;
-    const CT *y3;
-    CT *yout;
+    CT *y0;
+    CT *y2;
+    CT *y3;
+    CT *y4;
     const R *V0;
     const R *V1;
-    const int32_t *nbr;
-    const uint32_t *mask;
-    int64_t nb;
     R ihx2, ihy2, ihz2, g, dt;
     Ramp ramp;
+    double t_off;  // stage-0 time of this step relative to *ramp.clock
+    double dtd;    // dt in FP64 for stage times
 };
 
-template <typename R, int BX, int BY, int BZ, int ST, bool BLEND>
-__global__ void __launch_bounds__(256) k_rk4(const RkArgs<R> a)
+template <typename R, bool BLEND>
+__device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
 {
-    using B = Brick<BX, BY, BZ>;
+    if (!BLEND) return (R)0;
+    const double c = (st == 0) ? 0.0 : (st == 3 ? 1.0 : 0.5);
+    return (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + c * a.dtd);
+}
+
+// The warps of a block share the per-warp record slots below.
+constexpr int WARPS = 8;  // blocks of 256 threads, one brick per warp at a time
+
+// Minimum resident blocks per SM requested from the register allocator for
+// the stencil kernels (complex64 / complex128 bulk).
+#ifndef GPE_MINB_F
+#define GPE_MINB_F 2
+#endif
+#ifndef GPE_MINB_D
+#define GPE_MINB_D 1
+#endif
+#define GPE_BOUNDS(R) __launch_bounds__(256, (sizeof(R) == 4 ? GPE_MINB_F : GPE_MINB_D))
+
+// One RK4 stage on brick b, one warp, lane = segment within each group of 32.
+template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG>
+__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int st, int64_t b, BrickRec *Rr,
+                                          R s)
+{
+    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
-    __shared__ CT tile[B::TN];
-    R s = 0;
-    if (BLEND) s = (R)ramp_s(a.ramp, *a.ramp.clock + a.ramp.t_off);
-    const R c = (ST == 3) ? a.dt : (ST == 4 ? a.dt / (R)6 : a.dt / (R)2);
-    for (int64_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-        load_tile<BX, BY, BZ>(tile, a.yin, b, a.nbr, a.mask, [](CT v, int64_t) { return v; });
-        __syncthreads();
-        for (int l = threadIdx.x; l < B::BC; l += blockDim.x) {
-            const int64_t slot = b * B::BC + l;
-            if (!mask_bit(a.mask, slot)) continue;
-            const int x = l % BX, y = (l / BX) % BY, z = l / (BX * BY);
-            const CT L = tile_laplacian<BX, BY, BZ, R>(tile, x, y, z, a.ihx2, a.ihy2, a.ihz2);
-            const CT yc = tile[B::t(x, y, z)];
-            R V;
-            if (BLEND) V = ((R)1 - s) * a.V0[slot] + s * a.V1[slot];
-            else V = a.V0[slot];
-            const R w = V + a.g * (yc.x * yc.x + yc.y * yc.y);
-            const R hr = (R)(-0.5) * L.x + w * yc.x;
-            const R hi = (R)(-0.5) * L.y + w * yc.y;
-            CT o;  // f = -i (hr + i hi) = hi - i hr
-            if (ST == 1) {
-                o.x = yc.x + c * hi;
-                o.y = yc.y - c * hr;
-            } else if (ST < 4) {
-                const CT y0 = a.y0[slot];
-                o.x = y0.x + c * hi;
-                o.y = y0.y - c * hr;
-            } else {
-                const CT y0 = a.y0[slot], y2 = a.y2[slot], y3 = a.y3[slot];
-                o.x = (-y0.x + y2.x + (R)2 * y3.x + yc.x) / (R)3 + c * hi;
-                o.y = (-y0.y + y2.y + (R)2 * y3.y + yc.y) / (R)3 - c * hr;
+    const CT *yin = st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4;
+    CT *yout = st == 0 ? a.y2 : st == 1 ? a.y3 : st == 2 ? a.y4 : a.y0;
+    const R k = (st == 2) ? a.dt : (st == 3 ? a.dt / (R)6 : a.dt / (R)2);
+    load_recs(Rr, G, b);
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int it = 0; it < S::NIT; ++it) {
+        const int q = it * 32 + lane;
+        uint32_t idx = 0;
+        const bool stored = seg_index(Rr[0], q, idx);
+        R V0[4], V1[4];
+        CT y0[4], y2[4], y3[4];
+        if (stored) {
+            ldr4(a.V0 + idx, V0);
+            if (BLEND) ldr4(a.V1 + idx, V1);
+            if (st > 0) ld4<CG>(a.y0 + idx, y0);
+            if (st == 3) {
+                ld4<CG>(a.y2 + idx, y2);
+                ld4<CG>(a.y3 + idx, y3);
             }
-            a.yout[slot] = o;
         }
-        __syncthreads();
+        CT c[4], L[4];
+        gather<BX, BY, BZ, CG>(yin, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
+        if (!stored) continue;
+        CT o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (!(V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
+                o[i] = czero<CT>();
+                continue;
+            }
+            const R V = BLEND ? ((R)1 - s) * V0[i] + s * V1[i] : V0[i];
+            const R w = V + a.g * (c[i].x * c[i].x + c[i].y * c[i].y);
+            const R hr = (R)(-0.5) * L[i].x + w * c[i].x;
+            const R hi = (R)(-0.5) * L[i].y + w * c[i].y;
+            // f = -i (hr + i hi) = hi - i hr
+            if (st == 0) {
+                o[i].x = c[i].x + k * hi;
+                o[i].y = c[i].y - k * hr;
+            } else if (st < 3) {
+                o[i].x = y0[i].x + k * hi;
+                o[i].y = y0[i].y - k * hr;
+            } else {
+                o[i].x = (-y0[i].x + y2[i].x + (R)2 * y3[i].x + c[i].x) / (R)3 + k * hi;
+                o[i].y = (-y0[i].y + y2[i].y + (R)2 * y3[i].y + c[i].y) / (R)3 - k * hr;
+            }
+        }
+        st4(yout + idx, o);
     }
 }
 
-template <typename R, int BX, int BY, int BZ, int ST>
-static int launch_rk4(const gpe_grid *g, const RkArgs<R> &a, bool blend, cudaStream_t s)
+template <typename R, int BX, int BY, int BZ, bool BLEND>
+__global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G, int st)
 {
-    const int th = brick_threads(g);
-    if (blend) {
-        auto k = k_rk4<R, BX, BY, BZ, ST, true>;
-        k<<<blocks_for(k, g, th), th, 0, s>>>(a);
-    } else {
-        auto k = k_rk4<R, BX, BY, BZ, ST, false>;
-        k<<<blocks_for(k, g, th), th, 0, s>>>(a);
-    }
-    GPE_LAUNCH_CHECK();
-    return GPE_OK;
+    __shared__ BrickRec s_rec[WARPS][7];
+    const int warp = threadIdx.x >> 5;
+    const R s = stage_s<R, BLEND>(a, st);
+    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
+        rk4_brick<R, BX, BY, BZ, BLEND, false>(a, G, st, b, s_rec[warp], s);
 }
 
-template <typename R, int BX, int BY, int BZ>
-static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, double t0, cudaStream_t s)
+template <typename R, int BX, int BY, int BZ, bool BLEND>
+__global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, const Wave w)
 {
     using CT = typename Cx<R>::T;
-    const gpe_grid *g = st->grid;
-    const bool blend = p->potential == GPE_V_BLEND;
-    RkArgs<R> a{};
-    a.V0 = (const R *)potential_ptr(st, 0);
-    a.V1 = blend ? (const R *)potential_ptr(st, 1) : nullptr;
-    if (!a.V0 || (blend && !a.V1)) return fail(GPE_ERR_STATE, "potential slot missing");
-    a.nbr = g->d_nbr;
-    a.mask = g->d_mask;
-    a.nb = g->nb;
-    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
-    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
-    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
-    a.g = (R)p->g;
-    a.dt = (R)p->dt;
-    a.ramp.clock = st->d_clock;
-    a.ramp.T = p->T_ramp;
-    a.ramp.n_knots = p->n_knots;
-    for (int k = 0; k < GPE_MAX_KNOTS; ++k) a.ramp.knots[k] = p->knots[k];
-    CT *psi = (CT *)st->d_psi, *w0 = (CT *)st->d_work[0], *w1 = (CT *)st->d_work[1], *w2 = (CT *)st->d_work[2];
-    if (blend) {
-        k_set_scalar<<<1, 1, 0, s>>>(st->d_clock, t0);
-        GPE_LAUNCH_CHECK();
+    __shared__ BrickRec s_rec[WARPS][7];
+    const int warp = threadIdx.x >> 5;
+    R s[4];
+#pragma unroll
+    for (int st = 0; st < 4; ++st) s[st] = stage_s<R, BLEND>(a, st);
+    for (;;) {
+        const int task = next_task(w);
+        if (task < 0) break;
+        const int st = task >> 28, c = task & 0x0fffffff;
+        wait_for(w, st, c);
+        const int64_t b0 = (int64_t)c * w.cb;
+        const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
+        for (int64_t b = b0 + warp; b < b1; b += WARPS) rk4_brick<R, BX, BY, BZ, BLEND, true>(a, G, st, b, s_rec[warp], s[st]);
+        publish(w, st, c);
+        if (st == 3) {
+            // y2 and y3 of this chunk have no reader left in this step
+            const uint32_t p0 = __ldg(&G.rec[b0].off);
+            const uint32_t p1 = b1 < G.nb ? __ldg(&G.rec[b1].off) : w.n_packed;
+            discard_range(a.y2 + p0, (size_t)(p1 - p0) * sizeof(CT));
+            discard_range(a.y3 + p0, (size_t)(p1 - p0) * sizeof(CT));
+        }
     }
-    const double dt = p->dt;
-    for (int64_t n = 0; n < nsteps; ++n) {
-        const double tn = (double)n * dt;
-        a.yin = psi; a.y0 = psi; a.yout = w0; a.ramp.t_off = tn;
-        GPE_TRY((launch_rk4<R, BX, BY, BZ, 1>(g, a, blend, s)));
-        a.yin = w0; a.yout = w1; a.ramp.t_off = tn + 0.5 * dt;
-        GPE_TRY((launch_rk4<R, BX, BY, BZ, 2>(g, a, blend, s)));
-        a.yin = w1; a.yout = w2; a.ramp.t_off = tn + 0.5 * dt;
-        GPE_TRY((launch_rk4<R, BX, BY, BZ, 3>(g, a, blend, s)));
-        a.yin = w2; a.y2 = w0; a.y3 = w1; a.yout = psi; a.ramp.t_off = tn + dt;
-        GPE_TRY((launch_rk4<R, BX, BY, BZ, 4>(g, a, blend, s)));
-    }
-    return GPE_OK;
 }
 
 // ------------------------------------------------------------ imaginary time
-// Sec. II A/B, Eqs. (6)-(7).  K-ITP-A stages psi with its halo, applying on
-// load the pending renormalisation factor and the diagonal half step
-// psi * E * (1 - g|psi|^2 dt/2), E = exp(-V dt/2); then the first Euler
+// Sec. II A/B, Eqs. (6)-(7).  Stage A gathers psi with its neighbours,
+// applying on load the pending renormalisation factor and the diagonal half
+// step psi * E * (1 - g|psi|^2 dt/2), E = exp(-V dt/2); then the first Euler
 // kinetic substep psi - (dt/2) T psi = psi + (dt/4) lap psi -> tmp.
-// K-ITP-B stages tmp, takes the second Euler substep, applies the diagonal
-// half step again, writes psi and reduces sum |psi|^2 in FP64; the last block
-// stores the next factor sqrt(N / (sum |psi|^2 dV)).
+// Stage B gathers tmp, takes the second Euler substep, applies the diagonal
+// half step again, writes psi and sums |psi|^2 in FP64; the factor
+// sqrt(N / (sum |psi|^2 dV)) is stored for the next step's stage A (or the
+// end of the call).  E = 0 on inactive cells of stored segments (V = +inf),
+// so those stay zero.
 template <typename R>
 struct ItpArgs {
     using CT = typename Cx<R>::T;
-    const CT *in;
-    CT *out;
+    CT *psi;
+    CT *tmp;
     const R *E;
-    const int32_t *nbr;
-    const uint32_t *mask;
-    int64_t nb;
     R ihx2, ihy2, ihz2, g, dt;
     double *scalars;  // [0] scale to apply on load / next scale, [1] last norm
-    double *partials;
-    unsigned int *counter;
     double N, dV;
 };
 
-template <typename R, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(256) k_itp_a(const ItpArgs<R> a)
-{
-    using B = Brick<BX, BY, BZ>;
+template <typename R>
+struct DiagLoad {
     using CT = typename Cx<R>::T;
-    __shared__ CT tile[B::TN];
-    const R sc = (R)a.scalars[0];
-    const R hg = a.g * a.dt / (R)2;
-    const R q = a.dt / (R)4;
-    const R *E = a.E;
-    auto diag = [sc, hg, E](CT v, int64_t s) {
+    R sc, hg;
+    const R *E;
+    __device__ __forceinline__ CT operator()(CT v, uint32_t idx) const
+    {
         v.x *= sc;
         v.y *= sc;
-        const R f = E[s] * ((R)1 - hg * (v.x * v.x + v.y * v.y));
+        const R e = __ldg(E + idx);
+        const R f = e >= (R)0 ? e * ((R)1 - hg * (v.x * v.x + v.y * v.y)) : (R)0;
         v.x *= f;
         v.y *= f;
         return v;
-    };
-    for (int64_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-        load_tile<BX, BY, BZ>(tile, a.in, b, a.nbr, a.mask, diag);
-        __syncthreads();
-        for (int l = threadIdx.x; l < B::BC; l += blockDim.x) {
-            const int64_t slot = b * B::BC + l;
-            if (!mask_bit(a.mask, slot)) continue;
-            const int x = l % BX, y = (l / BX) % BY, z = l / (BX * BY);
-            const CT L = tile_laplacian<BX, BY, BZ, R>(tile, x, y, z, a.ihx2, a.ihy2, a.ihz2);
-            const CT yc = tile[B::t(x, y, z)];
-            CT o;
-            o.x = yc.x + q * L.x;
-            o.y = yc.y + q * L.y;
-            a.out[slot] = o;
+    }
+};
+
+template <typename R, int BX, int BY, int BZ, bool CG>
+__device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b, BrickRec *Rr, R sc)
+{
+    using S = Seg<BX, BY, BZ>;
+    using CT = typename Cx<R>::T;
+    const R q4 = a.dt / (R)4;
+    const DiagLoad<R> diag{sc, a.g * a.dt / (R)2, a.E};
+    load_recs(Rr, G, b);
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int it = 0; it < S::NIT; ++it) {
+        const int q = it * 32 + lane;
+        uint32_t idx = 0;
+        const bool stored = seg_index(Rr[0], q, idx);
+        R E[4];
+        if (stored) ldr4(a.E + idx, E);
+        CT c[4], L[4];
+        gather<BX, BY, BZ, CG>(a.psi, Rr, q, stored, idx, diag, a.ihx2, a.ihy2, a.ihz2, c, L);
+        if (!stored) continue;
+        CT o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool act = E[i] >= (R)0;  // E < 0 marks an inactive cell of a stored segment
+            o[i].x = act ? c[i].x + q4 * L[i].x : (R)0;
+            o[i].y = act ? c[i].y + q4 * L[i].y : (R)0;
         }
-        __syncthreads();
+        st4(a.tmp + idx, o);
+    }
+}
+
+template <typename R, int BX, int BY, int BZ, bool CG>
+__device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView &G, int64_t b, BrickRec *Rr,
+                                            double &acc)
+{
+    using S = Seg<BX, BY, BZ>;
+    using CT = typename Cx<R>::T;
+    const R hg = a.g * a.dt / (R)2;
+    const R q4 = a.dt / (R)4;
+    load_recs(Rr, G, b);
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int it = 0; it < S::NIT; ++it) {
+        const int q = it * 32 + lane;
+        uint32_t idx = 0;
+        const bool stored = seg_index(Rr[0], q, idx);
+        R E[4];
+        if (stored) ldr4(a.E + idx, E);
+        CT c[4], L[4];
+        gather<BX, BY, BZ, CG>(a.tmp, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
+        if (!stored) continue;
+        CT o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[i].x = c[i].x + q4 * L[i].x;
+            o[i].y = c[i].y + q4 * L[i].y;
+            const R f = E[i] >= (R)0 ? E[i] * ((R)1 - hg * (o[i].x * o[i].x + o[i].y * o[i].y)) : (R)0;
+            o[i].x *= f;
+            o[i].y *= f;
+            acc += (double)(o[i].x * o[i].x + o[i].y * o[i].y);
+        }
+        st4(a.psi + idx, o);
     }
 }
 
 template <typename R, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(256) k_itp_b(const ItpArgs<R> a)
+__global__ void GPE_BOUNDS(R) k_itp_a(const ItpArgs<R> a, const GridView G)
 {
-    using B = Brick<BX, BY, BZ>;
-    using CT = typename Cx<R>::T;
-    __shared__ CT tile[B::TN];
-    const R hg = a.g * a.dt / (R)2;
-    const R q = a.dt / (R)4;
+    __shared__ BrickRec s_rec[WARPS][7];
+    const int warp = threadIdx.x >> 5;
+    const R sc = (R)a.scalars[0];
+    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
+        itp_brick_a<R, BX, BY, BZ, false>(a, G, b, s_rec[warp], sc);
+}
+
+template <typename R, int BX, int BY, int BZ>
+__global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, double *partials,
+                                               unsigned int *counter)
+{
+    __shared__ BrickRec s_rec[WARPS][7];
+    const int warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
-    for (int64_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-        load_tile<BX, BY, BZ>(tile, a.in, b, a.nbr, a.mask, [](CT v, int64_t) { return v; });
-        __syncthreads();
-        for (int l = threadIdx.x; l < B::BC; l += blockDim.x) {
-            const int64_t slot = b * B::BC + l;
-            if (!mask_bit(a.mask, slot)) continue;
-            const int x = l % BX, y = (l / BX) % BY, z = l / (BX * BY);
-            const CT L = tile_laplacian<BX, BY, BZ, R>(tile, x, y, z, a.ihx2, a.ihy2, a.ihz2);
-            const CT yc = tile[B::t(x, y, z)];
-            CT o;
-            o.x = yc.x + q * L.x;
-            o.y = yc.y + q * L.y;
-            const R f = a.E[slot] * ((R)1 - hg * (o.x * o.x + o.y * o.y));
-            o.x *= f;
-            o.y *= f;
-            a.out[slot] = o;
-            acc[0] += (double)(o.x * o.x + o.y * o.y);
-        }
-        __syncthreads();
-    }
+    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
+        itp_brick_b<R, BX, BY, BZ, false>(a, G, b, s_rec[warp], acc[0]);
     double tot[1];
-    if (reduce_finish<1>(acc, a.partials, a.counter, tot) && threadIdx.x == 0) {
+    if (reduce_finish<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         const double nrm = tot[0] * a.dV;
         a.scalars[0] = sqrt(a.N / nrm);
         a.scalars[1] = nrm;
     }
 }
 
-template <typename CT>
-__global__ void k_apply_scale(CT *psi, const uint32_t *mask, int64_t ns, const double *scalars)
+// deterministic block sum (result valid in thread 0)
+__device__ __forceinline__ double block_sum(double x)
 {
-    const double sc = scalars[0];
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-        if ((mask[s >> 5] >> (s & 31)) & 1u) {
-            CT v = psi[s];
-            v.x = v.x * sc;
-            v.y = v.y * sc;
-            psi[s] = v;
+    __shared__ double sm[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    __syncthreads();
+    if (lane == 0) sm[warp] = x;
+    __syncthreads();
+    x = 0.0;
+    if (warp == 0) {
+        x = lane < nw ? sm[lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    }
+    return x;
+}
+
+template <typename R, int BX, int BY, int BZ>
+__global__ void GPE_BOUNDS(R) k_itp_wave(const ItpArgs<R> a, const GridView G, const Wave w,
+                                                  double *chunk_norm)
+{
+    __shared__ BrickRec s_rec[WARPS][7];
+    __shared__ bool s_last;
+    const int warp = threadIdx.x >> 5;
+    const R sc = (R)a.scalars[0];
+    for (;;) {
+        const int task = next_task(w);
+        if (task < 0) break;
+        const int st = task >> 28, c = task & 0x0fffffff;
+        wait_for(w, st, c);
+        const int64_t b0 = (int64_t)c * w.cb;
+        const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
+        if (st == 0) {
+            for (int64_t b = b0 + warp; b < b1; b += WARPS) itp_brick_a<R, BX, BY, BZ, true>(a, G, b, s_rec[warp], sc);
+            publish(w, st, c);
+            continue;
+        }
+        double acc = 0.0;
+        for (int64_t b = b0 + warp; b < b1; b += WARPS) itp_brick_b<R, BX, BY, BZ, true>(a, G, b, s_rec[warp], acc);
+        const double part = block_sum(acc);
+        if (threadIdx.x == 0) chunk_norm[c] = part;
+        publish(w, st, c);
+        if (threadIdx.x == 0) {
+            const unsigned long long k = atomicAdd(&w.ctr[1], 1ull) - w.finish_base;
+            s_last = (k == (unsigned long long)w.nchunks - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            // every chunk has finished both stages: fold the chunk norms in
+            // chunk order and store the next renormalisation factor
+            __threadfence();
+            double x = 0.0;
+            for (int i = threadIdx.x; i < w.nchunks; i += blockDim.x) x += __ldcg(chunk_norm + i);
+            x = block_sum(x);
+            if (threadIdx.x == 0) {
+                const double nrm = x * a.dV;
+                a.scalars[0] = sqrt(a.N / nrm);
+                a.scalars[1] = nrm;
+            }
         }
     }
 }
 
-template <typename R, int BX, int BY, int BZ>
-static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cudaStream_t s)
+template <typename CT>
+__global__ void k_apply_scale(CT *psi, int64_t n, const double *scalars)
 {
-    using CT = typename Cx<R>::T;
-    const gpe_grid *g = st->grid;
-    if (st->E_dt != p->dt) {
-        k_make_E<R><<<g->nsm * 8, 256, 0, s>>>(g->d_V[0], (R *)st->d_E, g->n_stored, p->dt);
-        GPE_LAUNCH_CHECK();
-        st->E_dt = p->dt;
+    const double sc = scalars[0];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        CT v = psi[s];
+        v.x = v.x * sc;
+        v.y = v.y * sc;
+        psi[s] = v;
     }
-    ItpArgs<R> a{};
-    a.E = (const R *)st->d_E;
-    a.nbr = g->d_nbr;
-    a.mask = g->d_mask;
-    a.nb = g->nb;
-    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
-    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
-    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
-    a.g = (R)p->g;
-    a.dt = (R)p->dt;
-    a.scalars = st->red.scalars;
-    a.partials = st->red.partials;
-    a.counter = st->red.counter;
-    a.N = p->N;
-    a.dV = g->box.hx * g->box.hy * g->box.hz;
-    CT *psi = (CT *)st->d_psi, *tmp = (CT *)st->d_work[0];
-    k_set_scalar<<<1, 1, 0, s>>>(st->red.scalars, 1.0);
-    GPE_LAUNCH_CHECK();
-    const int th = brick_threads(g);
-    auto ka = k_itp_a<R, BX, BY, BZ>;
-    auto kb = k_itp_b<R, BX, BY, BZ>;
-    const int nba = blocks_for(ka, g, th), nbb = blocks_for(kb, g, th);
-    for (int64_t n = 0; n < nsteps; ++n) {
-        a.in = psi;
-        a.out = tmp;
-        ka<<<nba, th, 0, s>>>(a);
-        GPE_LAUNCH_CHECK();
-        a.in = tmp;
-        a.out = psi;
-        kb<<<nbb, th, 0, s>>>(a);
-        GPE_LAUNCH_CHECK();
-    }
-    if (nsteps > 0) {
-        k_apply_scale<CT><<<g->nsm * 8, 256, 0, s>>>(psi, g->d_mask, g->n_stored, st->red.scalars);
-        GPE_LAUNCH_CHECK();
-    }
-    return GPE_OK;
 }
 
 // ------------------------------------------------------------ observables
@@ -394,9 +772,6 @@ struct ObsArgs {
     const R *V0;
     const R *V1;
     R s;
-    const int32_t *nbr;
-    const uint32_t *mask;
-    int64_t nb;
     R ihx2, ihy2, ihz2, g;
     double dV;
     double *partials;
@@ -405,30 +780,41 @@ struct ObsArgs {
 };
 
 template <typename R, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(256) k_obs(const ObsArgs<R> a)
+__global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R> a, const GridView G)
 {
-    using B = Brick<BX, BY, BZ>;
+    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
-    __shared__ CT tile[B::TN];
+    __shared__ BrickRec s_rec[WARPS][7];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // norm, ekin, epot, eint, nonfinite
-    for (int64_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-        load_tile<BX, BY, BZ>(tile, a.psi, b, a.nbr, a.mask, [](CT v, int64_t) { return v; });
-        __syncthreads();
-        for (int l = threadIdx.x; l < B::BC; l += blockDim.x) {
-            const int64_t slot = b * B::BC + l;
-            if (!mask_bit(a.mask, slot)) continue;
-            const int x = l % BX, y = (l / BX) % BY, z = l / (BX * BY);
-            const CT L = tile_laplacian<BX, BY, BZ, R>(tile, x, y, z, a.ihx2, a.ihy2, a.ihz2);
-            const CT yc = tile[B::t(x, y, z)];
-            const R V = a.V1 ? ((R)1 - a.s) * a.V0[slot] + a.s * a.V1[slot] : a.V0[slot];
-            const R rho = yc.x * yc.x + yc.y * yc.y;
-            acc[0] += (double)rho;
-            acc[1] += (double)((R)(-0.5) * (yc.x * L.x + yc.y * L.y));
-            acc[2] += (double)(V * rho);
-            acc[3] += (double)((R)0.5 * a.g * rho * rho);
-            acc[4] += (isfinite(yc.x) && isfinite(yc.y)) ? 0.0 : 1.0;
+    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS) {
+        BrickRec *Rr = s_rec[warp];
+        load_recs(Rr, G, b);
+#pragma unroll 1
+        for (int it = 0; it < S::NIT; ++it) {
+            const int q = it * 32 + lane;
+            uint32_t idx = 0;
+            const bool stored = seg_index(Rr[0], q, idx);
+            R V0[4], V1[4];
+            if (stored) {
+                ldr4(a.V0 + idx, V0);
+                if (a.V1) ldr4(a.V1 + idx, V1);
+            }
+            CT c[4], L[4];
+            gather<BX, BY, BZ, false>(a.psi, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
+            if (!stored) continue;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!(V0[i] < (R)INFINITY)) continue;
+                const R V = a.V1 ? ((R)1 - a.s) * V0[i] + a.s * V1[i] : V0[i];
+                const R rho = c[i].x * c[i].x + c[i].y * c[i].y;
+                acc[0] += (double)rho;
+                acc[1] += (double)((R)(-0.5) * (c[i].x * L[i].x + c[i].y * L[i].y));
+                acc[2] += (double)(V * rho);
+                acc[3] += (double)((R)0.5 * a.g * rho * rho);
+                acc[4] += (isfinite(c[i].x) && isfinite(c[i].y)) ? 0.0 : 1.0;
+            }
         }
-        __syncthreads();
     }
     double tot[5];
     if (reduce_finish<5>(acc, a.partials, a.counter, tot) && threadIdx.x == 0) {
@@ -444,47 +830,16 @@ __global__ void __launch_bounds__(256) k_obs(const ObsArgs<R> a)
     }
 }
 
-template <typename R, int BX, int BY, int BZ>
-static int obs_run(const gpe_state *stc, double gg, double sb, cudaStream_t s)
-{
-    gpe_state *st = const_cast<gpe_state *>(stc);
-    const gpe_grid *g = st->grid;
-    ObsArgs<R> a{};
-    a.psi = (const typename Cx<R>::T *)st->d_psi;
-    a.V0 = (const R *)potential_ptr(st, 0);
-    a.V1 = (sb != 0.0) ? (const R *)potential_ptr(st, 1) : nullptr;
-    if (sb != 0.0 && !a.V1) return fail(GPE_ERR_ARG, "s_blend != 0 needs potential slot 1");
-    a.s = (R)sb;
-    a.nbr = g->d_nbr;
-    a.mask = g->d_mask;
-    a.nb = g->nb;
-    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
-    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
-    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
-    a.g = (R)gg;
-    a.dV = g->box.hx * g->box.hy * g->box.hz;
-    a.partials = st->red.partials;
-    a.counter = st->red.counter;
-    a.out = (gpe_obs *)(st->red.scalars + 2);
-    const int th = brick_threads(g);
-    auto k = k_obs<R, BX, BY, BZ>;
-    k<<<blocks_for(k, g, th), th, 0, s>>>(a);
-    GPE_LAUNCH_CHECK();
-    return GPE_OK;
-}
-
-// <a|b> = sum conj(a) b dV
+// <a|b> = sum conj(a) b dV over the packed arrays (inactive entries are zero)
 template <typename CT>
-__global__ void k_overlap(const CT *a, const CT *b, const uint32_t *mask, int64_t ns, double dV, double *partials,
-                          unsigned int *counter, double *out)
+__global__ void k_overlap(const CT *a, const CT *b, int64_t n, double dV, double *partials, unsigned int *counter,
+                          double *out)
 {
     double acc[2] = {0.0, 0.0};
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-        if ((mask[s >> 5] >> (s & 31)) & 1u) {
-            const CT u = a[s], v = b[s];
-            acc[0] += (double)(u.x * v.x + u.y * v.y);
-            acc[1] += (double)(u.x * v.y - u.y * v.x);
-        }
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const CT u = a[s], v = b[s];
+        acc[0] += (double)(u.x * v.x + u.y * v.y);
+        acc[1] += (double)(u.x * v.y - u.y * v.x);
     }
     double tot[2];
     if (reduce_finish<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
@@ -499,51 +854,31 @@ struct BoxI {
     int BX, BY, BZ;
 };
 
-template <typename CT>
-__global__ void k_load_dense(const CT *dense, CT *psi, const int32_t *org, const uint32_t *mask, int64_t ns, BoxI b)
+template <typename CT, bool STORE>
+__global__ void k_dense_io(CT *psi, CT *dense, const int32_t *org, const uint32_t *mask, GridView G, int64_t ns,
+                           BoxI bi)
 {
-    const int BC = b.BX * b.BY * b.BZ;
+    const int BC = bi.BX * bi.BY * bi.BZ;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-        CT v;
-        v.x = 0;
-        v.y = 0;
-        if ((mask[s >> 5] >> (s & 31)) & 1u) {
-            const int64_t br = s / BC;
-            const int l = (int)(s % BC);
-            const int64_t i = org[3 * br] + l % b.BX, j = org[3 * br + 1] + (l / b.BX) % b.BY,
-                          k = org[3 * br + 2] + l / (b.BX * b.BY);
-            v = dense[i + b.nx * (j + b.ny * k)];
-        }
-        psi[s] = v;
+        if (!((mask[s >> 5] >> (s & 31)) & 1u)) continue;
+        const int64_t br = s / BC;
+        const int l = (int)(s % BC);
+        uint32_t idx;
+        if (!seg_index(G.rec[br], l >> 2, idx)) continue;  // cannot happen for an active cell
+        const int64_t i = org[3 * br] + l % bi.BX, j = org[3 * br + 1] + (l / bi.BX) % bi.BY,
+                      k = org[3 * br + 2] + l / (bi.BX * bi.BY);
+        const int64_t lin = i + bi.nx * (j + bi.ny * k);
+        if (STORE) dense[lin] = psi[idx + (l & 3)];
+        else psi[idx + (l & 3)] = dense[lin];
     }
 }
 
+// zero the inactive cells of stored segments (V0 = +inf there)
 template <typename CT>
-__global__ void k_store_dense(const CT *psi, CT *dense, const int32_t *org, const uint32_t *mask, int64_t ns, BoxI b)
+__global__ void k_zero_inactive(CT *psi, const double *V0, int64_t n)
 {
-    const int BC = b.BX * b.BY * b.BZ;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-        if ((mask[s >> 5] >> (s & 31)) & 1u) {
-            const int64_t br = s / BC;
-            const int l = (int)(s % BC);
-            const int64_t i = org[3 * br] + l % b.BX, j = org[3 * br + 1] + (l / b.BX) % b.BY,
-                          k = org[3 * br + 2] + l / (b.BX * b.BY);
-            dense[i + b.nx * (j + b.ny * k)] = psi[s];
-        }
-    }
-}
-
-template <typename CT>
-__global__ void k_mask_compact(CT *psi, const uint32_t *mask, int64_t ns)
-{
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-        if (!((mask[s >> 5] >> (s & 31)) & 1u)) {
-            CT v;
-            v.x = 0;
-            v.y = 0;
-            psi[s] = v;
-        }
-    }
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        if (!(V0[s] < INFINITY)) psi[s] = czero<CT>();
 }
 
 // ------------------------------------------------------------ state helpers
@@ -551,8 +886,8 @@ int ensure_work(gpe_state *st, int n)
 {
     for (int i = 0; i < n; ++i) {
         if (st->d_work[i]) continue;
-        GPE_TRY(dev_alloc(&st->d_work[i], st->grid->n_stored * st->elem));
-        GPE_TRY_CUDA(cudaMemset(st->d_work[i], 0, st->grid->n_stored * st->elem));
+        GPE_TRY(dev_alloc(&st->d_work[i], st->grid->n_packed * st->elem));
+        GPE_TRY_CUDA(cudaMemset(st->d_work[i], 0, st->grid->n_packed * st->elem));
     }
     return GPE_OK;
 }
@@ -576,6 +911,269 @@ static int check_state(const gpe_state *st)
     return GPE_OK;
 }
 
+// ------------------------------------------------------------ wavefront schedule
+// Chunk c = bricks [c*cb, (c+1)*cb).  lo/hi: the lowest and highest chunk that
+// holds a face neighbour of one of c's bricks (c included).  Task order: with
+// H(c) = max over c' <= c of hi(c'), tau(0, c) = c and
+// tau(s, c) = tau(s-1, H(c)) + 1; tasks sorted by (tau, s, c).  Every
+// dependency (s-1, c'), c' <= hi(c) <= H(c), then has a smaller tau, so it was
+// handed out earlier and the holder of the smallest unfinished ticket never
+// waits.
+static int build_schedule(gpe_grid *g)
+{
+    if (g->d_tasks) return GPE_OK;
+    // lag between a dependency's position and the task's: about one
+    // launch's worth of resident blocks, so that a task's dependencies were
+    // handed out a full wave of tasks earlier and have usually finished
+    int64_t lag = (int64_t)g->nsm * 2;
+    if (const char *e = getenv("GPE_WAVE_LAG")) lag = std::max<int64_t>(1, atoll(e));
+    const int64_t nb = g->nb, cb = g->cb;
+    const int64_t nch = (nb + cb - 1) / cb;
+    if (nch >= (1 << 28)) return fail(GPE_ERR_ARG, "too many chunks for the wavefront schedule");
+    std::vector<int32_t> nbr(nb * 6);
+    GPE_TRY_CUDA(cudaMemcpy(nbr.data(), g->d_nbr, nb * 6 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> lohi(nch * 2);
+    for (int64_t c = 0; c < nch; ++c) {
+        int64_t lo = c, hi = c;
+        for (int64_t b = c * cb; b < std::min(nb, (c + 1) * cb); ++b)
+            for (int d = 0; d < 6; ++d) {
+                const int32_t n = nbr[b * 6 + d];
+                if (n < 0) continue;
+                lo = std::min<int64_t>(lo, n / cb);
+                hi = std::max<int64_t>(hi, n / cb);
+            }
+        lohi[2 * c] = (int32_t)lo;
+        lohi[2 * c + 1] = (int32_t)hi;
+    }
+    std::vector<int64_t> H(nch);
+    int64_t run = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+        run = std::max<int64_t>(run, lohi[2 * c + 1]);
+        H[c] = run;
+    }
+    std::vector<int64_t> tau[4];
+    tau[0].resize(nch);
+    for (int64_t c = 0; c < nch; ++c) tau[0][c] = c;
+    for (int s = 1; s < 4; ++s) {
+        tau[s].resize(nch);
+        for (int64_t c = 0; c < nch; ++c) tau[s][c] = tau[s - 1][H[c]] + lag;
+    }
+    std::vector<int32_t> tasks;
+    tasks.reserve(6 * nch);
+    for (int S : {2, 4}) {
+        std::vector<std::pair<std::pair<int64_t, int>, int64_t>> v;
+        v.reserve(S * nch);
+        for (int s = 0; s < S; ++s)
+            for (int64_t c = 0; c < nch; ++c) v.push_back({{tau[s][c], s}, c});
+        std::sort(v.begin(), v.end());
+        for (auto &e : v) tasks.push_back((int32_t)((e.first.second << 28) | e.second));
+    }
+    int32_t *d_lohi = nullptr, *d_tasks = nullptr;
+    GPE_TRY(dev_alloc_t(&d_lohi, nch * 2));
+    int rc = dev_alloc_t(&d_tasks, tasks.size());
+    if (rc != GPE_OK) {
+        dev_free(d_lohi);
+        return rc;
+    }
+    if (cudaMemcpy(d_lohi, lohi.data(), lohi.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_tasks, tasks.data(), tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        dev_free(d_lohi);
+        dev_free(d_tasks);
+        return fail(GPE_ERR_CUDA, "schedule upload failed");
+    }
+    g->n_chunks = nch;
+    g->d_chunk_lohi = d_lohi;
+    g->d_tasks = d_tasks;
+    return GPE_OK;
+}
+
+static int ensure_wave(gpe_state *st)
+{
+    gpe_grid *g = st->grid;
+    GPE_TRY(build_schedule(g));
+    if (!st->d_done) {
+        GPE_TRY(dev_alloc_t(&st->d_done, g->n_chunks));
+        GPE_TRY_CUDA(cudaMemset(st->d_done, 0, g->n_chunks * sizeof(uint32_t)));
+        GPE_TRY(dev_alloc_t(&st->d_ctr, 4));
+        GPE_TRY_CUDA(cudaMemset(st->d_ctr, 0, 4 * sizeof(unsigned long long)));
+        GPE_TRY(dev_alloc_t(&st->d_chunk_norm, g->n_chunks));
+        st->epoch = 0;
+        st->ticket_base = 0;
+        st->finish_base = 0;
+    }
+    return GPE_OK;
+}
+
+static Wave make_wave(gpe_state *st, int stages)
+{
+    const gpe_grid *g = st->grid;
+    Wave w;
+    w.tasks = g->d_tasks + (stages == 2 ? 0 : 2 * g->n_chunks);
+    w.lohi = g->d_chunk_lohi;
+    w.done = st->d_done;
+    w.ctr = st->d_ctr;
+    w.ticket_base = st->ticket_base;
+    w.finish_base = st->finish_base;
+    w.epoch = st->epoch;
+    w.ntasks = (int)(stages * g->n_chunks);
+    w.cb = g->cb;
+    w.nchunks = (int)g->n_chunks;
+    w.n_packed = (uint32_t)g->n_packed;
+    return w;
+}
+
+// after a wave launch with `grid` blocks: every block took one ticket past
+// the end, so the counter advanced by ntasks + grid
+static void advance_wave(gpe_state *st, int stages, int grid_blocks, bool itp)
+{
+    st->ticket_base += (unsigned long long)stages * st->grid->n_chunks + (unsigned long long)grid_blocks;
+    if (itp) st->finish_base += (unsigned long long)st->grid->n_chunks;
+    st->epoch += (uint32_t)stages;
+}
+
+// ------------------------------------------------------------ step drivers
+template <typename R, int BX, int BY, int BZ>
+static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, double t0, cudaStream_t s)
+{
+    using CT = typename Cx<R>::T;
+    const gpe_grid *g = st->grid;
+    const bool blend = p->potential == GPE_V_BLEND;
+    RkArgs<R> a{};
+    a.V0 = (const R *)potential_ptr(st, 0);
+    a.V1 = blend ? (const R *)potential_ptr(st, 1) : nullptr;
+    if (!a.V0 || (blend && !a.V1)) return fail(GPE_ERR_STATE, "potential slot missing");
+    a.y0 = (CT *)st->d_psi;
+    a.y2 = (CT *)st->d_work[0];
+    a.y3 = (CT *)st->d_work[1];
+    a.y4 = (CT *)st->d_work[2];
+    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
+    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
+    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
+    a.g = (R)p->g;
+    a.dt = (R)p->dt;
+    a.dtd = p->dt;
+    a.ramp.clock = st->d_clock;
+    a.ramp.T = p->T_ramp;
+    a.ramp.n_knots = p->n_knots;
+    for (int k = 0; k < GPE_MAX_KNOTS; ++k) a.ramp.knots[k] = p->knots[k];
+    if (blend) {
+        k_set_scalar<<<1, 1, 0, s>>>(st->d_clock, t0);
+        GPE_LAUNCH_CHECK();
+    }
+    const GridView G = view(g);
+    const int th = brick_threads(g);
+    if (g->sched == GPE_SCHED_WAVE) {
+        GPE_TRY(ensure_wave(st));
+        auto k = blend ? k_rk4_wave<R, BX, BY, BZ, true> : k_rk4_wave<R, BX, BY, BZ, false>;
+        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th), 4 * g->n_chunks);
+        for (int64_t n = 0; n < nsteps; ++n) {
+            a.t_off = (double)n * p->dt;
+            k<<<nblk, th, 0, s>>>(a, G, make_wave(st, 4));
+            GPE_LAUNCH_CHECK();
+            advance_wave(st, 4, nblk, false);
+        }
+        return GPE_OK;
+    }
+    auto k = blend ? k_rk4_staged<R, BX, BY, BZ, true> : k_rk4_staged<R, BX, BY, BZ, false>;
+    const int nblk = blocks_for(k, g, th);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        a.t_off = (double)n * p->dt;
+        for (int stg = 0; stg < 4; ++stg) {
+            k<<<nblk, th, 0, s>>>(a, G, stg);
+            GPE_LAUNCH_CHECK();
+        }
+    }
+    return GPE_OK;
+}
+
+template <typename R, int BX, int BY, int BZ>
+static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cudaStream_t s)
+{
+    using CT = typename Cx<R>::T;
+    const gpe_grid *g = st->grid;
+    if (st->E_dt != p->dt) {
+        k_make_E<R><<<g->nsm * 8, 256, 0, s>>>(g->d_V[0], (R *)st->d_E, g->n_packed, p->dt);
+        GPE_LAUNCH_CHECK();
+        st->E_dt = p->dt;
+    }
+    ItpArgs<R> a{};
+    a.psi = (CT *)st->d_psi;
+    a.tmp = (CT *)st->d_work[0];
+    a.E = (const R *)st->d_E;
+    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
+    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
+    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
+    a.g = (R)p->g;
+    a.dt = (R)p->dt;
+    a.scalars = st->red.scalars;
+    a.N = p->N;
+    a.dV = g->box.hx * g->box.hy * g->box.hz;
+    k_set_scalar<<<1, 1, 0, s>>>(st->red.scalars, 1.0);
+    GPE_LAUNCH_CHECK();
+    const GridView G = view(g);
+    const int th = brick_threads(g);
+    if (g->sched == GPE_SCHED_WAVE) {
+        GPE_TRY(ensure_wave(st));
+        auto k = k_itp_wave<R, BX, BY, BZ>;
+        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th), 2 * g->n_chunks);
+        for (int64_t n = 0; n < nsteps; ++n) {
+            k<<<nblk, th, 0, s>>>(a, G, make_wave(st, 2), st->d_chunk_norm);
+            GPE_LAUNCH_CHECK();
+            advance_wave(st, 2, nblk, true);
+        }
+    } else {
+        auto ka = k_itp_a<R, BX, BY, BZ>;
+        auto kb = k_itp_b<R, BX, BY, BZ>;
+        const int nba = blocks_for(ka, g, th), nbb = blocks_for(kb, g, th);
+        for (int64_t n = 0; n < nsteps; ++n) {
+            ka<<<nba, th, 0, s>>>(a, G);
+            GPE_LAUNCH_CHECK();
+            kb<<<nbb, th, 0, s>>>(a, G, st->red.partials, st->red.counter);
+            GPE_LAUNCH_CHECK();
+        }
+    }
+    k_apply_scale<CT><<<g->nsm * 8, 256, 0, s>>>((CT *)st->d_psi, g->n_packed, st->red.scalars);
+    GPE_LAUNCH_CHECK();
+    return GPE_OK;
+}
+
+template <typename R, int BX, int BY, int BZ>
+static int obs_run(const gpe_state *stc, double gg, double sb, cudaStream_t s)
+{
+    gpe_state *st = const_cast<gpe_state *>(stc);
+    const gpe_grid *g = st->grid;
+    ObsArgs<R> a{};
+    a.psi = (const typename Cx<R>::T *)st->d_psi;
+    a.V0 = (const R *)potential_ptr(st, 0);
+    a.V1 = (sb != 0.0) ? (const R *)potential_ptr(st, 1) : nullptr;
+    if (sb != 0.0 && !a.V1) return fail(GPE_ERR_ARG, "s_blend != 0 needs potential slot 1");
+    a.s = (R)sb;
+    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
+    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
+    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
+    a.g = (R)gg;
+    a.dV = g->box.hx * g->box.hy * g->box.hz;
+    a.partials = st->red.partials;
+    a.counter = st->red.counter;
+    a.out = (gpe_obs *)(st->red.scalars + 2);
+    const int th = brick_threads(g);
+    auto k = k_obs<R, BX, BY, BZ>;
+    k<<<blocks_for(k, g, th), th, 0, s>>>(a, view(g));
+    GPE_LAUNCH_CHECK();
+    return GPE_OK;
+}
+
+// device error word of the wavefront schedule (0 = fine)
+static int wave_error(const gpe_state *st, cudaStream_t s)
+{
+    if (!st->d_ctr) return GPE_OK;
+    unsigned long long e = 0;
+    GPE_TRY_CUDA(cudaMemcpyAsync(&e, st->d_ctr + 2, sizeof e, cudaMemcpyDeviceToHost, s));
+    GPE_TRY_CUDA(cudaStreamSynchronize(s));
+    if (e) return fail(GPE_ERR_CUDA, "a wavefront dependency wait timed out (results are invalid)");
+    return GPE_OK;
+}
+
 }  // namespace gpe
 
 using namespace gpe;
@@ -590,10 +1188,10 @@ extern "C" int gpe_state_create(gpe_grid *g, int dtype, gpe_state **out)
     st->grid = g;
     st->dtype = dtype;
     st->elem = dtype == GPE_C128 ? 16 : 8;
-    int rc = dev_alloc(&st->d_psi, g->n_stored * st->elem);
-    if (rc == GPE_OK && cudaMemset(st->d_psi, 0, g->n_stored * st->elem) != cudaSuccess)
+    int rc = dev_alloc(&st->d_psi, g->n_packed * st->elem);
+    if (rc == GPE_OK && cudaMemset(st->d_psi, 0, g->n_packed * st->elem) != cudaSuccess)
         rc = fail(GPE_ERR_CUDA, "cudaMemset(psi) failed");
-    if (rc == GPE_OK) rc = dev_alloc(&st->d_E, g->n_stored * st->elem / 2);
+    if (rc == GPE_OK) rc = dev_alloc(&st->d_E, g->n_packed * st->elem / 2);
     if (rc == GPE_OK) rc = dev_alloc_t(&st->d_clock, 1);
     if (rc == GPE_OK) rc = red_alloc(st->red, g->nsm * 32);
     if (rc == GPE_OK && cudaMallocHost(&st->h_obs, sizeof(gpe_obs)) != cudaSuccess)
@@ -620,6 +1218,9 @@ extern "C" int gpe_state_destroy(gpe_state *st)
     for (int i = 0; i < 3; ++i) dev_free(st->d_work[i]);
     dev_free(st->d_E);
     dev_free(st->d_clock);
+    dev_free(st->d_done);
+    dev_free(st->d_ctr);
+    dev_free(st->d_chunk_norm);
     red_free(st->red);
     if (st->h_obs) cudaFreeHost(st->h_obs);
     st->grid->n_states--;
@@ -641,17 +1242,20 @@ extern "C" int gpe_state_load(gpe_state *st, const void *psi, int layout, int on
     if (!psi) return fail(GPE_ERR_ARG, "psi is NULL");
     const gpe_grid *g = st->grid;
     cudaStream_t s = S(stream);
-    const BoxI bi{g->box.nx, g->box.ny, g->box.nz, g->bx, g->by, g->bz};
+    const GridView G = view(g);
     if (layout == GPE_LAYOUT_COMPACT) {
-        GPE_TRY_CUDA(cudaMemcpyAsync(st->d_psi, psi, g->n_stored * st->elem,
+        GPE_TRY_CUDA(cudaMemcpyAsync(st->d_psi, psi, g->n_packed * st->elem,
                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        if (st->dtype == GPE_C128) k_mask_compact<double2><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, g->d_mask, g->n_stored);
-        else k_mask_compact<float2><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, g->d_mask, g->n_stored);
+        if (st->dtype == GPE_C128)
+            k_zero_inactive<double2><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, g->d_V[0], g->n_packed);
+        else
+            k_zero_inactive<float2><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, g->d_V[0], g->n_packed);
         GPE_LAUNCH_CHECK();
         if (!on_device) GPE_TRY_CUDA(cudaStreamSynchronize(s));
         return GPE_OK;
     }
     if (layout != GPE_LAYOUT_DENSE) return fail(GPE_ERR_ARG, "unknown layout %d", layout);
+    const BoxI bi{g->box.nx, g->box.ny, g->box.nz, g->bx, g->by, g->bz};
     const size_t dbytes = (size_t)g->box.nx * g->box.ny * g->box.nz * st->elem;
     const void *src = psi;
     void *owned = nullptr;
@@ -664,16 +1268,22 @@ extern "C" int gpe_state_load(gpe_state *st, const void *psi, int layout, int on
         }
         src = owned;
     }
-    if (st->dtype == GPE_C128)
-        k_load_dense<double2><<<g->nsm * 8, 256, 0, s>>>((const double2 *)src, (double2 *)st->d_psi, g->d_org, g->d_mask, g->n_stored, bi);
-    else
-        k_load_dense<float2><<<g->nsm * 8, 256, 0, s>>>((const float2 *)src, (float2 *)st->d_psi, g->d_org, g->d_mask, g->n_stored, bi);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(st->d_psi, 0, g->n_packed * st->elem, s);
+    if (e == cudaSuccess) {
+        if (st->dtype == GPE_C128)
+            k_dense_io<double2, false><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, (double2 *)src, g->d_org, g->d_mask, G,
+                                                                 g->n_stored, bi);
+        else
+            k_dense_io<float2, false><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, (float2 *)src, g->d_org, g->d_mask, G,
+                                                                g->n_stored, bi);
+        count_launch();
+        e = cudaGetLastError();
+    }
     if (owned) {
         cudaStreamSynchronize(s);
         dev_free(owned);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "k_load_dense", __FILE__, __LINE__);
+    if (e != cudaSuccess) return cuda_fail(e, "gpe_state_load", __FILE__, __LINE__);
     return GPE_OK;
 }
 
@@ -683,8 +1293,9 @@ extern "C" int gpe_state_store(const gpe_state *st, void *psi, int layout, int o
     if (!psi) return fail(GPE_ERR_ARG, "psi is NULL");
     const gpe_grid *g = st->grid;
     cudaStream_t s = S(stream);
+    GPE_TRY(wave_error(st, s));
     if (layout == GPE_LAYOUT_COMPACT) {
-        GPE_TRY_CUDA(cudaMemcpyAsync(psi, st->d_psi, g->n_stored * st->elem,
+        GPE_TRY_CUDA(cudaMemcpyAsync(psi, st->d_psi, g->n_packed * st->elem,
                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         if (!on_device) GPE_TRY_CUDA(cudaStreamSynchronize(s));
         return GPE_OK;
@@ -698,12 +1309,16 @@ extern "C" int gpe_state_store(const gpe_state *st, void *psi, int layout, int o
         GPE_TRY(dev_alloc(&owned, dbytes));
         dst = owned;
     }
+    const GridView G = view(g);
     cudaError_t e = cudaMemsetAsync(dst, 0, dbytes, s);
     if (e == cudaSuccess) {
         if (st->dtype == GPE_C128)
-            k_store_dense<double2><<<g->nsm * 8, 256, 0, s>>>((const double2 *)st->d_psi, (double2 *)dst, g->d_org, g->d_mask, g->n_stored, bi);
+            k_dense_io<double2, true><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, (double2 *)dst, g->d_org, g->d_mask, G,
+                                                                g->n_stored, bi);
         else
-            k_store_dense<float2><<<g->nsm * 8, 256, 0, s>>>((const float2 *)st->d_psi, (float2 *)dst, g->d_org, g->d_mask, g->n_stored, bi);
+            k_dense_io<float2, true><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, (float2 *)dst, g->d_org, g->d_mask, G,
+                                                               g->n_stored, bi);
+        count_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && owned) e = cudaMemcpyAsync(psi, owned, dbytes, cudaMemcpyDeviceToHost, s);
@@ -722,7 +1337,8 @@ extern "C" int gpe_state_copy(gpe_state *dst, const gpe_state *src, gpe_stream s
     GPE_TRY(check_state(src));
     if (dst->grid != src->grid || dst->dtype != src->dtype)
         return fail(GPE_ERR_ARG, "states differ in grid or dtype");
-    GPE_TRY_CUDA(cudaMemcpyAsync(dst->d_psi, src->d_psi, src->grid->n_stored * src->elem, cudaMemcpyDeviceToDevice, S(stream)));
+    GPE_TRY_CUDA(cudaMemcpyAsync(dst->d_psi, src->d_psi, src->grid->n_packed * src->elem, cudaMemcpyDeviceToDevice,
+                                 S(stream)));
     return GPE_OK;
 }
 
@@ -794,6 +1410,7 @@ extern "C" int gpe_observables(const gpe_state *st, double g, double s_blend, gp
     if (rc != GPE_OK) return rc;
     GPE_TRY_CUDA(cudaMemcpyAsync(st->h_obs, st->red.scalars + 2, sizeof(gpe_obs), cudaMemcpyDeviceToHost, s));
     GPE_TRY_CUDA(cudaStreamSynchronize(s));
+    GPE_TRY(wave_error(st, s));
     *out = *st->h_obs;
     if (out->nonfinite > 0) return fail(GPE_ERR_NONFINITE, "%.0f active cells hold NaN or Inf", out->nonfinite);
     return GPE_OK;
@@ -811,11 +1428,11 @@ extern "C" int gpe_overlap(const gpe_state *a, const gpe_state *b, double out[2]
     const int blocks = g->nsm * 4;
     const double dV = g->box.hx * g->box.hy * g->box.hz;
     if (a->dtype == GPE_C128)
-        k_overlap<double2><<<blocks, 256, 0, s>>>((const double2 *)a->d_psi, (const double2 *)b->d_psi, g->d_mask,
-                                                   g->n_stored, dV, w->red.partials, w->red.counter, w->red.scalars + 10);
+        k_overlap<double2><<<blocks, 256, 0, s>>>((const double2 *)a->d_psi, (const double2 *)b->d_psi, g->n_packed,
+                                                   dV, w->red.partials, w->red.counter, w->red.scalars + 10);
     else
-        k_overlap<float2><<<blocks, 256, 0, s>>>((const float2 *)a->d_psi, (const float2 *)b->d_psi, g->d_mask,
-                                                  g->n_stored, dV, w->red.partials, w->red.counter, w->red.scalars + 10);
+        k_overlap<float2><<<blocks, 256, 0, s>>>((const float2 *)a->d_psi, (const float2 *)b->d_psi, g->n_packed, dV,
+                                                  w->red.partials, w->red.counter, w->red.scalars + 10);
     GPE_LAUNCH_CHECK();
     double h[2];
     GPE_TRY_CUDA(cudaMemcpyAsync(h, w->red.scalars + 10, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -34,7 +34,8 @@ ERROR_NAMES = {v: k for k, v in dict(
     GPE_ERR_UNSTABLE=-5, GPE_ERR_NOT_CONVERGED=-6, GPE_ERR_STATE=-7).items()}
 
 GPE_MASK_CELL, GPE_MASK_BRICK = 0, 1
-GPE_ORDER_MORTON, GPE_ORDER_ZMAJOR = 0, 1
+GPE_ORDER_ZMAJOR, GPE_ORDER_MORTON = 0, 1
+GPE_SCHED_STAGED, GPE_SCHED_WAVE = 0, 1
 GPE_F64, GPE_F32 = 1, 2
 GPE_POT_HARMONIC, GPE_POT_ELLIPSOID_SHELL = 1, 2
 GPE_C128, GPE_C64 = 1, 2
@@ -53,7 +54,8 @@ class gpe_box(C.Structure):
 
 class gpe_grid_opts(C.Structure):
     _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32),
-                ("mask_mode", C.c_int32), ("order", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("mask_mode", C.c_int32), ("order", C.c_int32), ("sched", C.c_int32),
+                ("chunk", C.c_int32), ("reserved", C.c_int32)]
 
 
 class gpe_potential(C.Structure):
@@ -62,7 +64,7 @@ class gpe_potential(C.Structure):
 
 class gpe_grid_info(C.Structure):
     _fields_ = [("n_active", C.c_int64), ("n_bricks", C.c_int64), ("n_stored", C.c_int64),
-                ("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32), ("mask_mode", C.c_int32),
+                ("n_packed", C.c_int64), ("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32), ("mask_mode", C.c_int32),
                 ("order", C.c_int32), ("n_slots", C.c_int32), ("v_max", C.c_double),
                 ("box", gpe_box)]
 
@@ -219,12 +221,43 @@ def make_box(nx, ny, nz, hx, hy=None, hz=None, x0=None, y0=None, z0=None) -> gpe
     return gpe_box(nx, ny, nz, hx, hy, hz, x0, y0, z0)
 
 
-def make_opts(brick=(8, 8, 8), mask_mode=GPE_MASK_CELL, order=GPE_ORDER_MORTON) -> gpe_grid_opts:
+def make_opts(brick=(8, 8, 8), mask_mode=GPE_MASK_CELL, order=GPE_ORDER_ZMAJOR, sched=GPE_SCHED_STAGED,
+              chunk=0) -> gpe_grid_opts:
     o = gpe_grid_opts()
     o.bx, o.by, o.bz = brick
     o.mask_mode = mask_mode
     o.order = order
+    o.sched = sched
+    o.chunk = chunk
     return o
+
+
+def packed_layout(grid):
+    """Host-side map of the compact layout: (packed index, brick, local cell)
+    of every active cell, from the brick list and the mask, by the rule of
+    include/gpe.h (each brick stores, in order, its 4-cell x-segments that
+    hold an active cell)."""
+    info = gpe_grid_get_info(grid)
+    bits = gpe_grid_mask(grid)
+    bc = info.bx * info.by * info.bz
+    act = np.unpackbits(bits.view(np.uint8), bitorder="little").astype(bool).reshape(info.n_bricks, bc)
+    seg = act.reshape(info.n_bricks, bc // 4, 4).any(axis=2)
+    nseg = seg.sum(axis=1)
+    off = 4 * np.concatenate([[0], np.cumsum(nseg)[:-1]]).astype(np.int64)
+    seg_rank = np.cumsum(seg, axis=1) - 1
+    b, l = np.nonzero(act)
+    return off[b] + 4 * seg_rank[b, l // 4] + (l % 4), b, l
+
+
+def packed_coords(grid):
+    """(packed index, i, j, k) of every active cell."""
+    info = gpe_grid_get_info(grid)
+    org, _ = gpe_grid_bricks(grid)
+    idx, b, l = packed_layout(grid)
+    i = org[b, 0] + l % info.bx
+    j = org[b, 1] + (l // info.bx) % info.by
+    k = org[b, 2] + l // (info.bx * info.by)
+    return idx, i, j, k
 
 
 def make_potential(kind, *params) -> gpe_potential:
@@ -310,7 +343,7 @@ def gpe_grid_mask(grid):
 
 def gpe_grid_potential(grid, slot=0):
     info = gpe_grid_get_info(grid)
-    V = np.empty(info.n_stored, dtype=np.float64)
+    V = np.empty(info.n_packed, dtype=np.float64)
     _check(load().gpe_grid_potential(grid, int(slot), V.ctypes.data))
     return V
 

@@ -71,4 +71,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gpe.gpe_potential) == 8 + 8 * 8
     assert ctypes.sizeof(gpe.gpe_real_params) == 2 * 8 + 4 * 4 + 8 + 16 * 8
     assert ctypes.sizeof(gpe.gpe_obs) == 7 * 8
-    assert ctypes.sizeof(gpe.gpe_grid_info) == 3 * 8 + 6 * 4 + 8 + ctypes.sizeof(gpe.gpe_box)
+    assert ctypes.sizeof(gpe.gpe_grid_info) == 4 * 8 + 6 * 4 + 8 + ctypes.sizeof(gpe.gpe_box)

@@ -43,7 +43,7 @@ def test_noalloc_overlap_matches_gpe_overlap_twice(dtype, tol):
         gpe.gpe_state_load(a, np.ascontiguousarray(case.psi.astype(cdt)), gpe.GPE_LAYOUT_DENSE)
         other = inputs.random_state(case.box.shape, seed=9).astype(cdt)
         gpe.gpe_state_load(b, np.ascontiguousarray(other), gpe.GPE_LAYOUT_DENSE)
-        n = gpe.gpe_grid_get_info(grid).n_stored
+        n = gpe.gpe_grid_get_info(grid).n_packed
         pa, pb = gpe.gpe_state_device_ptr(a), gpe.gpe_state_device_ptr(b)
         ref = gpe.gpe_overlap(a, b)
         for _ in range(2):
