@@ -220,6 +220,13 @@ int gpe_state_store(const gpe_state *st, void *psi, int layout, int on_device,
 /* dst <- src (same grid and dtype).  Asynchronous. */
 int gpe_state_copy(gpe_state *dst, const gpe_state *src, gpe_stream stream);
 
+/* Step loops on the staged schedule are captured in CUDA graphs of
+ * steps_per_graph steps (default 32; 0 disables) and replayed, when the
+ * stream is not the legacy default stream and a call asks for at least that
+ * many steps; each distinct parameter set is captured once per state.  The
+ * wavefront schedule always launches directly. */
+int gpe_state_set_graph(gpe_state *st, int steps_per_graph);
+
 /* Device pointer of the compact psi array (borrowed; valid until destroy). */
 int gpe_state_device_ptr(gpe_state *st, void **dptr);
 
@@ -318,6 +325,52 @@ int gpe_overlap_noalloc(const void *a, const void *b, int64_t n, int dtype,
 int gpe_ground_state(gpe_state *st, const gpe_imag_params *p, double tol_dmu,
                      int64_t check_every, int64_t max_steps,
                      int64_t *steps_done, gpe_obs *obs, gpe_stream stream);
+
+/* ------------------------------------------------------------------ batches */
+/* Many independent shells in one persistent launch (one launch of each kernel
+ * covers every shell of the batch).  The states must share the state type and
+ * brick shape; their grids may differ in size, spacing and potential.  The
+ * batch copies the states' tables and keeps them alive; destroy the batch
+ * before the states' grids. */
+int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out);
+
+/* Imaginary-time ground states of every shell of the batch (Sec. II A,
+ * Eqs. (6)-(7); per-shell g, dt, N from per_shell[i]): blocks of check_every
+ * steps, each captured once in a CUDA graph and replayed, followed by FP64
+ * observables and the test |mu - mu_prev| < tol_dmu against the previous
+ * check; a converged shell stops stepping while the others continue.  Stops
+ * when every shell converged or after max_steps.  On return each state holds
+ * its result; converged[i], steps[i] and obs[i] (any may be NULL) report each
+ * shell.  GPE_ERR_NOT_CONVERGED if a shell did not converge,
+ * GPE_ERR_NONFINITE if one produced NaN/Inf (it is stopped).  Synchronous. */
+int gpe_batch_ground_state(gpe_batch *batch, const gpe_imag_params *per_shell,
+                           double tol_dmu, int64_t check_every,
+                           int64_t max_steps, int32_t *converged,
+                           int64_t *steps, gpe_obs *obs, gpe_stream stream);
+
+int gpe_batch_destroy(gpe_batch *batch);
+
+/* ------------------------------------------------------------------ tuning */
+enum { GPE_TUNE_REAL = 0, GPE_TUNE_IMAG = 1 };
+typedef struct gpe_tune_result {
+    int32_t bx, by, bz, sched, chunk, reserved;
+    double cell_steps_per_s; /* active-cell-steps per second */
+    double ms_per_step;
+} gpe_tune_result;
+
+/* Time every candidate layout (brick 8x8x8, 8x8x4, 8x4x4) and schedule
+ * (staged; wavefront with 2-8 bricks per task) on the grid that
+ * gpe_grid_create_analytic(box, pot, V_cut) builds, for `nsteps` real-time
+ * (RK4) or imaginary-time steps of a state of type dtype, and return the
+ * fastest in *best (use its fields in gpe_grid_opts).  all (room for 8
+ * entries, may be NULL) receives every timing and *n_all their number.
+ * Results are cached per device, state type, step kind and size class
+ * (n_active within a factor sqrt(2)); with all == NULL a cached answer is
+ * returned without timing (*n_all = 0).  Synchronous; allocates temporary
+ * grids. */
+int gpe_autotune(const gpe_box *box, const gpe_potential *pot, double V_cut,
+                 int dtype, int mode, int nsteps, gpe_tune_result *best,
+                 gpe_tune_result *all, int *n_all, gpe_stream stream);
 
 #ifdef __cplusplus
 }

@@ -51,6 +51,15 @@ void dev_free(void *p)
     if (p) cudaFree(p);
 }
 
+// Zero freshly allocated memory and wait for it: the caller's stream may be a
+// non-blocking stream that does not order itself after the legacy stream.
+int dev_zero(void *p, size_t bytes)
+{
+    GPE_TRY_CUDA(cudaMemsetAsync(p, 0, bytes, cudaStreamLegacy));
+    GPE_TRY_CUDA(cudaStreamSynchronize(cudaStreamLegacy));
+    return GPE_OK;
+}
+
 int shape_id(int bx, int by, int bz)
 {
     if (bx == 8 && by == 8 && bz == 8) return 0;
@@ -76,8 +85,8 @@ int red_alloc(RedScratch &r, int max_blocks)
     GPE_TRY(dev_alloc_t(&r.partials, (size_t)max_blocks * 8));
     GPE_TRY(dev_alloc_t(&r.counter, 1));
     GPE_TRY(dev_alloc_t(&r.scalars, 16));
-    GPE_TRY_CUDA(cudaMemset(r.counter, 0, sizeof(unsigned int)));
-    GPE_TRY_CUDA(cudaMemset(r.scalars, 0, 16 * sizeof(double)));
+    GPE_TRY(dev_zero(r.counter, sizeof(unsigned int)));
+    GPE_TRY(dev_zero(r.scalars, 16 * sizeof(double)));
     r.max_blocks = max_blocks;
     return GPE_OK;
 }

@@ -58,6 +58,7 @@ inline int dev_alloc_t(T **p, size_t count)
     return dev_alloc(reinterpret_cast<void **>(p), count * sizeof(T));
 }
 void dev_free(void *p);
+int dev_zero(void *p, size_t bytes);  // memset 0 and wait (any stream may use it next)
 
 inline cudaStream_t S(gpe_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -323,6 +324,12 @@ struct gpe_state {
     double *d_chunk_norm = nullptr;       // per-chunk FP64 partial norms (ITP)
     uint32_t epoch = 0;                   // stages completed so far (flags compare to it)
     unsigned long long ticket_base = 0, finish_base = 0;
+    // CUDA graphs of `graph_steps` staged steps ([0] real time, [1] imaginary)
+    int graph_steps = 32;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    unsigned long long gkey[2] = {0, 0};
+    int gnodes[2] = {0, 0};
+    cudaStream_t gcap = nullptr;
 };
 
 namespace gpe {

@@ -675,8 +675,7 @@ extern "C" int gpe_grid_set_potential(gpe_grid *g, int slot, const void *V, int 
     int rc = GPE_OK;
     if (!g->d_V[slot]) {
         rc = dev_alloc_t(&g->d_V[slot], g->n_packed);
-        if (rc == GPE_OK && cudaMemset(g->d_V[slot], 0, g->n_packed * sizeof(double)) != cudaSuccess)
-            rc = fail(GPE_ERR_CUDA, "cudaMemset(V) failed");
+        if (rc == GPE_OK) rc = dev_zero(g->d_V[slot], g->n_packed * sizeof(double));
     }
     if (rc == GPE_OK) {
         k_set_potential<<<(unsigned)g->nb, std::min(g->bc, 256), 0, st>>>(dptr, V_dtype, boxd(g->box), g->bx,

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "gpe_internal.cuh"
+#include "stencil.cuh"
 
 namespace gpe {
 
@@ -94,238 +95,7 @@ static int blocks_for(K kernel, const gpe_grid *g, int threads)
 
 static inline int brick_threads(const gpe_grid *) { return 256; }
 
-#define GPE_SHAPES(M) \
-    M(0, 8, 8, 8)     \
-    M(1, 8, 8, 4)     \
-    M(2, 8, 4, 4)
 
-// ------------------------------------------------------------ packed layout
-struct GridView {
-    const int32_t *nbr;
-    const BrickRec *rec;
-    int64_t nb;
-};
-
-static GridView view(const gpe_grid *g) { return GridView{g->d_nbr, g->d_rec, g->nb}; }
-
-// segment geometry of a brick shape (BX must be 8: two segments per row)
-template <int BX, int BY, int BZ>
-struct Seg {
-    static_assert(BX == 8, "bricks are 8 cells long in x");
-    static constexpr int SX = BX / 4;          // segments per x-row
-    static constexpr int PLANE = SX * BY;      // segments per z-plane (divides 32)
-    static constexpr int NSEG = PLANE * BZ;    // segments per brick
-    static constexpr int NIT = NSEG / 32;      // warp iterations per brick
-    static_assert(32 % PLANE == 0 && NSEG % 32 == 0, "brick shape must tile the warp");
-};
-
-template <typename CT>
-__device__ __forceinline__ CT czero()
-{
-    CT z;
-    z.x = 0;
-    z.y = 0;
-    return z;
-}
-
-__device__ __forceinline__ float2 shfl_up(float2 v, int d)
-{
-    v.x = __shfl_up_sync(0xffffffffu, v.x, d);
-    v.y = __shfl_up_sync(0xffffffffu, v.y, d);
-    return v;
-}
-__device__ __forceinline__ double2 shfl_up(double2 v, int d)
-{
-    v.x = __shfl_up_sync(0xffffffffu, v.x, d);
-    v.y = __shfl_up_sync(0xffffffffu, v.y, d);
-    return v;
-}
-__device__ __forceinline__ float2 shfl_down(float2 v, int d)
-{
-    v.x = __shfl_down_sync(0xffffffffu, v.x, d);
-    v.y = __shfl_down_sync(0xffffffffu, v.y, d);
-    return v;
-}
-__device__ __forceinline__ double2 shfl_down(double2 v, int d)
-{
-    v.x = __shfl_down_sync(0xffffffffu, v.x, d);
-    v.y = __shfl_down_sync(0xffffffffu, v.y, d);
-    return v;
-}
-__device__ __forceinline__ float2 shfl_xor(float2 v, int d)
-{
-    v.x = __shfl_xor_sync(0xffffffffu, v.x, d);
-    v.y = __shfl_xor_sync(0xffffffffu, v.y, d);
-    return v;
-}
-__device__ __forceinline__ double2 shfl_xor(double2 v, int d)
-{
-    v.x = __shfl_xor_sync(0xffffffffu, v.x, d);
-    v.y = __shfl_xor_sync(0xffffffffu, v.y, d);
-    return v;
-}
-
-// 4 consecutive complex values (one segment); CG: read through L2 only
-// (data written by other blocks of the same launch)
-template <bool CG>
-__device__ __forceinline__ void ld4(const float2 *p, float2 (&v)[4])
-{
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-    const float4 a = CG ? __ldcg(q) : q[0], b = CG ? __ldcg(q + 1) : q[1];
-    v[0] = make_float2(a.x, a.y);
-    v[1] = make_float2(a.z, a.w);
-    v[2] = make_float2(b.x, b.y);
-    v[3] = make_float2(b.z, b.w);
-}
-template <bool CG>
-__device__ __forceinline__ void ld4(const double2 *p, double2 (&v)[4])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = CG ? __ldcg(p + i) : p[i];
-}
-__device__ __forceinline__ void st4(float2 *p, const float2 (&v)[4])
-{
-    float4 *q = reinterpret_cast<float4 *>(p);
-    q[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    q[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-}
-__device__ __forceinline__ void st4(double2 *p, const double2 (&v)[4])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) p[i] = v[i];
-}
-__device__ __forceinline__ void ldr4(const float *p, float (&v)[4])
-{
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = a.z;
-    v[3] = a.w;
-}
-__device__ __forceinline__ void ldr4(const double *p, double (&v)[4])
-{
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-}
-
-struct Identity {
-    template <typename CT>
-    __device__ __forceinline__ CT operator()(CT v, uint32_t) const { return v; }
-};
-
-// Records of brick b (slot 0) and of its six face neighbours (slots 1..6,
-// order -x +x -y +y -z +z; an absent neighbour gets an empty record), loaded by
-// one warp into its shared-memory slots.
-__device__ __forceinline__ void load_recs(BrickRec *R, const GridView &G, int64_t b)
-{
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
-    if (lane < 7) {
-        const int64_t id = lane == 0 ? b : (int64_t)__ldg(&G.nbr[b * 6 + lane - 1]);
-        uint4 a = make_uint4(0, 0, 0, 0), c = make_uint4(0, 0, 0, 0);
-        if (id >= 0) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(G.rec + id);
-            a = __ldg(p);
-            c = __ldg(p + 1);
-        }
-        uint4 *d = reinterpret_cast<uint4 *>(R + lane);
-        d[0] = a;
-        d[1] = c;
-    }
-    __syncwarp();
-}
-
-// One lane's segment q of a brick: its four values c[] and their 7-point
-// Laplacians L[] (Eq. (B1)), every loaded value passed through xf first.
-// All 32 lanes must call this together: x and y neighbours inside the brick
-// come from other lanes by shuffles; z neighbours and brick-boundary
-// neighbours are loaded.  Every load of the lane is issued before the first
-// shuffle so that they are in flight together.
-template <bool CG, typename CT>
-__device__ __forceinline__ CT ld1(const CT *p)
-{
-    return CG ? __ldcg(p) : *p;
-}
-
-template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF>
-__device__ __forceinline__ void gather(const CT *src, const BrickRec *Rr, int q, bool stored, uint32_t idx, XF xf,
-                                       R ihx2, R ihy2, R ihz2, CT (&c)[4], CT (&L)[4])
-{
-    using S = Seg<BX, BY, BZ>;
-    const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-    // neighbour segments that live in memory
-    uint32_t jzm = 0, jzp = 0, jy = 0, jx = 0;
-    const bool hzm = stored && (z == 0 ? seg_index(Rr[5], q + S::PLANE * (BZ - 1), jzm)
-                                       : seg_index(Rr[0], q - S::PLANE, jzm));
-    const bool hzp = stored && (z == BZ - 1 ? seg_index(Rr[6], q - S::PLANE * (BZ - 1), jzp)
-                                            : seg_index(Rr[0], q + S::PLANE, jzp));
-    const bool ylo = (y == 0), yhi = (y == BY - 1);
-    const bool hy = stored && (ylo ? seg_index(Rr[3], hx + S::SX * (BY - 1) + S::PLANE * z, jy)
-                                   : (yhi && seg_index(Rr[4], hx + S::PLANE * z, jy)));
-    // x: segment (1, y, z) of the -x brick (cell x = 7) or (0, y, z) of the +x brick (cell x = 0)
-    const bool hxb = stored && (hx == 0 ? seg_index(Rr[1], q + 1, jx) : seg_index(Rr[2], q - 1, jx));
-    if (hx == 0) jx += 3;
-    CT zm[4], zp[4], yb[4], xb = czero<CT>();
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] = zm[i] = zp[i] = yb[i] = czero<CT>();
-    if (stored) ld4<CG>(src + idx, c);
-    if (hzm) ld4<CG>(src + jzm, zm);
-    if (hzp) ld4<CG>(src + jzp, zp);
-    if (hy) ld4<CG>(src + jy, yb);
-    if (hxb) xb = ld1<CG>(src + jx);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (stored) c[i] = xf(c[i], idx + i);
-        if (hzm) zm[i] = xf(zm[i], jzm + i);
-        if (hzp) zp[i] = xf(zp[i], jzp + i);
-        if (hy) yb[i] = xf(yb[i], jy + i);
-    }
-    if (hxb) xb = xf(xb, jx);
-    CT ym[4], yp[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        ym[i] = shfl_up(c[i], S::SX);
-        yp[i] = shfl_down(c[i], S::SX);
-        if (ylo) ym[i] = yb[i];
-        if (yhi) yp[i] = yb[i];
-    }
-    const CT p0 = shfl_xor(c[0], 1), p3 = shfl_xor(c[3], 1);
-    const CT xm = hx == 0 ? xb : p3;  // left of cell 0
-    const CT xp = hx == 0 ? p0 : xb;  // right of cell 3
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const CT l = i == 0 ? xm : c[i - 1];
-        const CT r = i == 3 ? xp : c[i + 1];
-        L[i].x = (r.x - 2 * c[i].x + l.x) * ihx2 + (yp[i].x - 2 * c[i].x + ym[i].x) * ihy2 +
-                 (zp[i].x - 2 * c[i].x + zm[i].x) * ihz2;
-        L[i].y = (r.y - 2 * c[i].y + l.y) * ihx2 + (yp[i].y - 2 * c[i].y + ym[i].y) * ihy2 +
-                 (zp[i].y - 2 * c[i].y + zm[i].y) * ihz2;
-    }
-}
-
-// ------------------------------------------------------------ ramp schedule
-struct Ramp {
-    const double *clock;  // device time base
-    double T;
-    int n_knots;
-    double knots[GPE_MAX_KNOTS];
-};
-
-// s(t): piecewise linear through n_knots values at t_k = k T/(n_knots-1),
-// held constant outside [0, T] (linear interpolation between potentials, Sec. V)
-__device__ __forceinline__ double ramp_s(const Ramp &r, double t)
-{
-    if (t <= 0.0) return r.knots[0];
-    if (t >= r.T) return r.knots[r.n_knots - 1];
-    double u = t / r.T * (double)(r.n_knots - 1);
-    int k = (int)floor(u);
-    if (k >= r.n_knots - 1) k = r.n_knots - 2;
-    double w = u - (double)k;
-    return (1.0 - w) * r.knots[k] + w * r.knots[k + 1];
-}
 
 // ------------------------------------------------------------ wavefront sync
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
@@ -451,19 +221,6 @@ __device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
     return (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + c * a.dtd);
 }
 
-// The warps of a block share the per-warp record slots below.
-constexpr int WARPS = 8;  // blocks of 256 threads, one brick per warp at a time
-
-// Minimum resident blocks per SM requested from the register allocator for
-// the stencil kernels (complex64 / complex128 bulk).
-#ifndef GPE_MINB_F
-#define GPE_MINB_F 2
-#endif
-#ifndef GPE_MINB_D
-#define GPE_MINB_D 1
-#endif
-#define GPE_BOUNDS(R) __launch_bounds__(256, (sizeof(R) == 4 ? GPE_MINB_F : GPE_MINB_D))
-
 // One RK4 stage on brick b, one warp, lane = segment within each group of 32.
 template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG>
 __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int st, int64_t b, BrickRec *Rr,
@@ -581,23 +338,6 @@ struct ItpArgs {
     double N, dV;
 };
 
-template <typename R>
-struct DiagLoad {
-    using CT = typename Cx<R>::T;
-    R sc, hg;
-    const R *E;
-    __device__ __forceinline__ CT operator()(CT v, uint32_t idx) const
-    {
-        v.x *= sc;
-        v.y *= sc;
-        const R e = __ldg(E + idx);
-        const R f = e >= (R)0 ? e * ((R)1 - hg * (v.x * v.x + v.y * v.y)) : (R)0;
-        v.x *= f;
-        v.y *= f;
-        return v;
-    }
-};
-
 template <typename R, int BX, int BY, int BZ, bool CG>
 __device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b, BrickRec *Rr, R sc)
 {
@@ -687,23 +427,6 @@ __global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, doub
         a.scalars[0] = sqrt(a.N / nrm);
         a.scalars[1] = nrm;
     }
-}
-
-// deterministic block sum (result valid in thread 0)
-__device__ __forceinline__ double block_sum(double x)
-{
-    __shared__ double sm[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    __syncthreads();
-    if (lane == 0) sm[warp] = x;
-    __syncthreads();
-    x = 0.0;
-    if (warp == 0) {
-        x = lane < nw ? sm[lane] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    }
-    return x;
 }
 
 template <typename R, int BX, int BY, int BZ>
@@ -887,7 +610,7 @@ int ensure_work(gpe_state *st, int n)
     for (int i = 0; i < n; ++i) {
         if (st->d_work[i]) continue;
         GPE_TRY(dev_alloc(&st->d_work[i], st->grid->n_packed * st->elem));
-        GPE_TRY_CUDA(cudaMemset(st->d_work[i], 0, st->grid->n_packed * st->elem));
+        GPE_TRY(dev_zero(st->d_work[i], st->grid->n_packed * st->elem));
     }
     return GPE_OK;
 }
@@ -993,9 +716,9 @@ static int ensure_wave(gpe_state *st)
     GPE_TRY(build_schedule(g));
     if (!st->d_done) {
         GPE_TRY(dev_alloc_t(&st->d_done, g->n_chunks));
-        GPE_TRY_CUDA(cudaMemset(st->d_done, 0, g->n_chunks * sizeof(uint32_t)));
+        GPE_TRY(dev_zero(st->d_done, g->n_chunks * sizeof(uint32_t)));
         GPE_TRY(dev_alloc_t(&st->d_ctr, 4));
-        GPE_TRY_CUDA(cudaMemset(st->d_ctr, 0, 4 * sizeof(unsigned long long)));
+        GPE_TRY(dev_zero(st->d_ctr, 4 * sizeof(unsigned long long)));
         GPE_TRY(dev_alloc_t(&st->d_chunk_norm, g->n_chunks));
         st->epoch = 0;
         st->ticket_base = 0;
@@ -1030,6 +753,56 @@ static void advance_wave(gpe_state *st, int stages, int grid_blocks, bool itp)
     if (itp) st->finish_base += (unsigned long long)st->grid->n_chunks;
     st->epoch += (uint32_t)stages;
 }
+
+// ------------------------------------------------------------ CUDA graphs
+static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+// Graphs replay on the caller's stream; the legacy default stream cannot be
+// captured, so steps issued there run eagerly.
+static bool use_graph(const gpe_state *st, cudaStream_t s, int64_t nsteps)
+{
+    return st->graph_steps > 0 && nsteps >= st->graph_steps && s != nullptr && s != cudaStreamLegacy &&
+           s != cudaStreamPerThread;
+}
+
+// Replay graph `which` (capturing it first if its key changed) `reps` times.
+template <typename F>
+static int replay_graph(gpe_state *st, int which, uint64_t key, int nodes, int64_t reps, cudaStream_t s, F record)
+{
+    if (!st->gexec[which] || st->gkey[which] != key) {
+        if (st->gexec[which]) {
+            cudaGraphExecDestroy(st->gexec[which]);
+            st->gexec[which] = nullptr;
+        }
+        if (!st->gcap) GPE_TRY_CUDA(cudaStreamCreateWithFlags(&st->gcap, cudaStreamNonBlocking));
+        GPE_TRY_CUDA(cudaStreamBeginCapture(st->gcap, cudaStreamCaptureModeThreadLocal));
+        const int rc = record(st->gcap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st->gcap, &graph);
+        if (rc != GPE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        const cudaError_t e2 = cudaGraphInstantiate(&st->gexec[which], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate", __FILE__, __LINE__);
+        st->gkey[which] = key;
+        st->gnodes[which] = nodes;
+    }
+    for (int64_t r = 0; r < reps; ++r) {
+        GPE_TRY_CUDA(cudaGraphLaunch(st->gexec[which], s));
+        for (int k = 0; k < nodes; ++k) count_launch();
+    }
+    return GPE_OK;
+}
+
+__global__ void k_add_scalar(double *p, double v) { *p += v; }
 
 // ------------------------------------------------------------ step drivers
 template <typename R, int BX, int BY, int BZ>
@@ -1076,14 +849,36 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
     }
     auto k = blend ? k_rk4_staged<R, BX, BY, BZ, true> : k_rk4_staged<R, BX, BY, BZ, false>;
     const int nblk = blocks_for(k, g, th);
-    for (int64_t n = 0; n < nsteps; ++n) {
-        a.t_off = (double)n * p->dt;
-        for (int stg = 0; stg < 4; ++stg) {
-            k<<<nblk, th, 0, s>>>(a, G, stg);
-            GPE_LAUNCH_CHECK();
+    // steps n0 .. n0+cnt-1 with stage times relative to the device clock
+    auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
+        for (int64_t n = 0; n < cnt; ++n) {
+            a.t_off = (double)n * p->dt;
+            for (int stg = 0; stg < 4; ++stg) {
+                k<<<nblk, th, 0, cs>>>(a, G, stg);
+                GPE_LAUNCH_CHECK();
+            }
         }
+        return GPE_OK;
+    };
+    int64_t left = nsteps;
+    if (use_graph(st, s, nsteps)) {
+        const int G_ = st->graph_steps;
+        uint64_t key = fnv1a(p, sizeof *p);
+        const void *ptrs[2] = {a.V0, a.V1};
+        key = fnv1a(ptrs, sizeof ptrs, key);
+        key = fnv1a(&G_, sizeof G_, key);
+        auto rec_block = [&](cudaStream_t cs) -> int {
+            GPE_TRY(record(cs, G_));
+            if (blend) {
+                k_add_scalar<<<1, 1, 0, cs>>>(st->d_clock, (double)G_ * p->dt);
+                GPE_LAUNCH_CHECK();
+            }
+            return GPE_OK;
+        };
+        GPE_TRY(replay_graph(st, 0, key, 4 * G_ + (blend ? 1 : 0), nsteps / G_, s, rec_block));
+        left = nsteps % G_;
     }
-    return GPE_OK;
+    return record(s, left);
 }
 
 template <typename R, int BX, int BY, int BZ>
@@ -1125,12 +920,25 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
         auto ka = k_itp_a<R, BX, BY, BZ>;
         auto kb = k_itp_b<R, BX, BY, BZ>;
         const int nba = blocks_for(ka, g, th), nbb = blocks_for(kb, g, th);
-        for (int64_t n = 0; n < nsteps; ++n) {
-            ka<<<nba, th, 0, s>>>(a, G);
-            GPE_LAUNCH_CHECK();
-            kb<<<nbb, th, 0, s>>>(a, G, st->red.partials, st->red.counter);
-            GPE_LAUNCH_CHECK();
+        auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
+            for (int64_t n = 0; n < cnt; ++n) {
+                ka<<<nba, th, 0, cs>>>(a, G);
+                GPE_LAUNCH_CHECK();
+                kb<<<nbb, th, 0, cs>>>(a, G, st->red.partials, st->red.counter);
+                GPE_LAUNCH_CHECK();
+            }
+            return GPE_OK;
+        };
+        int64_t left = nsteps;
+        if (use_graph(st, s, nsteps)) {
+            const int G_ = st->graph_steps;
+            uint64_t key = fnv1a(p, sizeof *p);
+            key = fnv1a(&G_, sizeof G_, key);
+            key = fnv1a(&a.E, sizeof a.E, key);
+            GPE_TRY(replay_graph(st, 1, key, 2 * G_, nsteps / G_, s, [&](cudaStream_t cs) { return record(cs, G_); }));
+            left = nsteps % G_;
         }
+        GPE_TRY(record(s, left));
     }
     k_apply_scale<CT><<<g->nsm * 8, 256, 0, s>>>((CT *)st->d_psi, g->n_packed, st->red.scalars);
     GPE_LAUNCH_CHECK();
@@ -1189,8 +997,7 @@ extern "C" int gpe_state_create(gpe_grid *g, int dtype, gpe_state **out)
     st->dtype = dtype;
     st->elem = dtype == GPE_C128 ? 16 : 8;
     int rc = dev_alloc(&st->d_psi, g->n_packed * st->elem);
-    if (rc == GPE_OK && cudaMemset(st->d_psi, 0, g->n_packed * st->elem) != cudaSuccess)
-        rc = fail(GPE_ERR_CUDA, "cudaMemset(psi) failed");
+    if (rc == GPE_OK) rc = dev_zero(st->d_psi, g->n_packed * st->elem);
     if (rc == GPE_OK) rc = dev_alloc(&st->d_E, g->n_packed * st->elem / 2);
     if (rc == GPE_OK) rc = dev_alloc_t(&st->d_clock, 1);
     if (rc == GPE_OK) rc = red_alloc(st->red, g->nsm * 32);
@@ -1221,10 +1028,21 @@ extern "C" int gpe_state_destroy(gpe_state *st)
     dev_free(st->d_done);
     dev_free(st->d_ctr);
     dev_free(st->d_chunk_norm);
+    for (int i = 0; i < 2; ++i)
+        if (st->gexec[i]) cudaGraphExecDestroy(st->gexec[i]);
+    if (st->gcap) cudaStreamDestroy(st->gcap);
     red_free(st->red);
     if (st->h_obs) cudaFreeHost(st->h_obs);
     st->grid->n_states--;
     delete st;
+    return GPE_OK;
+}
+
+extern "C" int gpe_state_set_graph(gpe_state *st, int steps_per_graph)
+{
+    GPE_TRY(check_state(st));
+    if (steps_per_graph < 0 || steps_per_graph > 4096) return fail(GPE_ERR_ARG, "steps_per_graph must be in [0, 4096]");
+    st->graph_steps = steps_per_graph;
     return GPE_OK;
 }
 

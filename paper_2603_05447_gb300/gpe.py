@@ -86,6 +86,18 @@ class gpe_obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gpe_tune_result(C.Structure):
+    _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32), ("sched", C.c_int32),
+                ("chunk", C.c_int32), ("reserved", C.c_int32), ("cell_steps_per_s", C.c_double),
+                ("ms_per_step", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+GPE_TUNE_REAL, GPE_TUNE_IMAG = 0, 1
+
+
 class GpeError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
@@ -126,6 +138,13 @@ _SIGS = {
     "gpe_step_real": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, _P]),
     "gpe_observables": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(gpe_obs), _P]),
     "gpe_overlap": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P]),
+    "gpe_state_set_graph": (C.c_int, [_P, C.c_int]),
+    "gpe_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P)]),
+    "gpe_batch_ground_state": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_double, C.c_int64, C.c_int64,
+                                         C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(gpe_obs), _P]),
+    "gpe_batch_destroy": (C.c_int, [_P]),
+    "gpe_autotune": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.c_double, C.c_int, C.c_int, C.c_int,
+                               C.POINTER(gpe_tune_result), C.POINTER(gpe_tune_result), C.POINTER(C.c_int), _P]),
     "gpe_overlap_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_double), _P]),
     "gpe_ground_state": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_double, C.c_int64, C.c_int64,
                                    C.POINTER(C.c_int64), C.POINTER(gpe_obs), _P]),
@@ -417,6 +436,44 @@ def gpe_overlap(a, b, stream=None) -> complex:
     out = (C.c_double * 2)()
     _check(load().gpe_overlap(a, b, out, stream_handle(stream)))
     return complex(out[0], out[1])
+
+
+def gpe_state_set_graph(state, steps_per_graph):
+    _check(load().gpe_state_set_graph(state, int(steps_per_graph)))
+
+
+def gpe_batch_create(states):
+    arr = (_P * len(states))(*states)
+    out = _P()
+    _check(load().gpe_batch_create(arr, len(states), C.byref(out)))
+    return out.value
+
+
+def gpe_batch_ground_state(batch, per_shell, tol_dmu, check_every, max_steps, stream=None, check=True):
+    """Returns (rc, converged[n], steps[n], obs list of dicts)."""
+    n = len(per_shell)
+    params = (gpe_imag_params * n)(*per_shell)
+    conv = (C.c_int32 * n)()
+    steps = (C.c_int64 * n)()
+    obs = (gpe_obs * n)()
+    rc = load().gpe_batch_ground_state(batch, params, float(tol_dmu), int(check_every), int(max_steps), conv, steps,
+                                       obs, stream_handle(stream))
+    if check and rc != GPE_OK:
+        raise GpeError(rc, last_error())
+    return rc, list(conv), list(steps), [o.asdict() for o in obs]
+
+
+def gpe_batch_destroy(batch):
+    _check(load().gpe_batch_destroy(batch))
+
+
+def gpe_autotune(box, pot, V_cut, dtype, mode, nsteps, timings=True, stream=None):
+    best = gpe_tune_result()
+    allr = (gpe_tune_result * 8)()
+    n = C.c_int()
+    _check(load().gpe_autotune(C.byref(box), C.byref(pot), float(V_cut), int(dtype), int(mode), int(nsteps),
+                               C.byref(best), allr if timings else None, C.byref(n), stream_handle(stream)))
+    return best.asdict(), [allr[i].asdict() for i in range(n.value)]
 
 
 def gpe_overlap_noalloc(a, b, n, dtype, dV, stream=None) -> complex:

@@ -1,0 +1,184 @@
+"""Batched shells in one persistent launch, CUDA-graph step loops and the
+autotuner, through the C ABI, against the FP64 oracle and the single-state
+path."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_05447_gb300 import gpe, inputs
+
+from gpu_cases import harmonic64, shell, ragged_shell, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2603_05447_gb300 import _build
+    _build.build()
+    torch.cuda.init()
+    torch.cuda.set_device(0)
+    return gpe.load()
+
+
+def make(case, dtype=gpe.GPE_C128, brick=(8, 8, 8)):
+    grid = gpe.gpe_grid_create_dense(case.gbox, case.V, case.V_cut, gpe.make_opts(brick))
+    st = gpe.gpe_state_create(grid, dtype)
+    cdt = np.complex128 if dtype == gpe.GPE_C128 else np.complex64
+    gpe.gpe_state_load(st, np.ascontiguousarray(case.psi.astype(cdt)), gpe.GPE_LAYOUT_DENSE)
+    return grid, st
+
+
+def dense(case, st, dtype=gpe.GPE_C128):
+    out = np.zeros(case.box.shape, np.complex128 if dtype == gpe.GPE_C128 else np.complex64)
+    gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_DENSE)
+    return out.astype(np.complex128)
+
+
+def shell_cases():
+    """Uneven shells: different box sizes, spacings, couplings."""
+    wl2 = inputs.ShellWorkload(n=48, a_cells=20.0, g=800.0)
+    c2 = shell(wl2, seed=5)
+    return [shell(), ragged_shell(), c2, harmonic64(g=30.0)]
+
+
+def test_batch_fixed_steps_match_oracle_per_shell():
+    cases = shell_cases()
+    made = [make(c) for c in cases]
+    batch = gpe.gpe_batch_create([st for _, st in made])
+    try:
+        params = [gpe.gpe_imag_params(c.g, c.dt, 1.0) for c in cases]
+        # a tolerance no shell can meet: every shell runs exactly max_steps
+        rc, conv, steps, obs = gpe.gpe_batch_ground_state(batch, params, 1e-300, 5, 15, check=False)
+        assert rc == gpe.GPE_ERR_NOT_CONVERGED
+        assert steps == [15] * len(cases) and not any(conv)
+        for c, (_, st), o in zip(cases, made, obs):
+            og = oracle.Grid(c.mask, (c.box.hx, c.box.hy, c.box.hz))
+            y = og.compact(c.psi)
+            for _ in range(15):
+                y, _ = oracle.itp_step(og, og.compact(c.V), y, c.g, c.dt, 1.0)
+            assert rel_l2(dense(c, st), og.dense(y)) <= 1e-12, c.name
+            ref = oracle.observables(og, og.compact(c.V), c.g, y)
+            assert abs(o["mu"] - ref["mu"]) <= 1e-11 * abs(ref["mu"])
+            assert abs(o["norm"] - 1.0) <= 1e-12
+    finally:
+        gpe.gpe_batch_destroy(batch)
+        for g, st in made:
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(g)
+
+
+def trap_cases():
+    """Harmonic traps of uneven sizes and couplings (their ground states
+    converge within a few thousand steps at dt = 1e-3)."""
+    from gpu_cases import Case
+    out = []
+    for n, h, g in ((64, 0.25, 30.0), (48, 0.3, 100.0), (40, 0.35, 0.0)):
+        box = inputs.cubic_box(n, h)
+        V = inputs.dense_potential(box, inputs.Harmonic(1.0, 1.1, 0.9))
+        psi = inputs.gaussian_with_noise(box, seed=n, noise=1e-3)
+        out.append(Case(f"trap{n}", box, V, 12.0, psi, g, 1e-3))
+    return out
+
+
+@pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64])
+def test_batch_convergence_matches_single_state_solver(dtype):
+    cases = trap_cases()
+    made = [make(c, dtype) for c in cases]
+    solo = [make(c, dtype) for c in cases]
+    batch = gpe.gpe_batch_create([st for _, st in made])
+    try:
+        params = [gpe.gpe_imag_params(c.g, c.dt, 1.0) for c in cases]
+        tol = 1e-7 if dtype == gpe.GPE_C128 else 1e-5
+        rc, conv, steps, obs = gpe.gpe_batch_ground_state(batch, params, tol, 50, 20000)
+        assert len(set(steps)) > 1                  # the shells stopped at different checks
+        assert rc == gpe.GPE_OK and all(conv)
+        for c, (_, st), (_, st1), n, o, p in zip(cases, made, solo, steps, obs, params):
+            n1, o1 = gpe.gpe_ground_state(st1, p, tol, 50, 20000)
+            assert n1 == n                       # same checks, same stopping step
+            tol_mu = 1e-10 if dtype == gpe.GPE_C128 else 1e-6
+            assert abs(o["mu"] - o1["mu"]) <= tol_mu * abs(o1["mu"])
+            tol_l2 = 1e-10 if dtype == gpe.GPE_C128 else 1e-5
+            assert rel_l2(dense(c, st, dtype), dense(c, st1, dtype)) <= tol_l2
+    finally:
+        gpe.gpe_batch_destroy(batch)
+        for g, st in made + solo:
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(g)
+
+
+def test_graph_replay_matches_eager_steps_bit_for_bit():
+    case = ragged_shell()
+    g1, eager = make(case)
+    g2, graphed = make(case)
+    try:
+        gpe.gpe_state_set_graph(graphed, 4)
+        side = torch.cuda.Stream()
+        p = gpe.real_params(case.g, case.dt)
+        gpe.gpe_step_real(eager, p, 11, stream=0)
+        with torch.cuda.stream(side):
+            gpe.gpe_step_real(graphed, p, 11, stream=side)      # 2 replays of 4 + 3 eager
+            gpe.gpe_step_real(graphed, p, 8, stream=side)       # cached graph, 2 replays
+        torch.cuda.synchronize()
+        gpe.gpe_step_real(eager, p, 8, stream=0)
+        assert np.array_equal(dense(case, eager), dense(case, graphed))
+        ip = gpe.gpe_imag_params(case.g, case.dt, 1.0)
+        gpe.gpe_step_imag(eager, ip, 9, stream=0)
+        with torch.cuda.stream(side):
+            gpe.gpe_step_imag(graphed, ip, 9, stream=side)
+        torch.cuda.synchronize()
+        assert rel_l2(dense(case, graphed), dense(case, eager)) <= 1e-15
+    finally:
+        for g, st in ((g1, eager), (g2, graphed)):
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(g)
+
+
+def test_graph_replay_of_ramp_matches_oracle():
+    from gpu_cases import ramp_case
+    case = ramp_case()
+    ind = np.where(case.region, -1.0, 1.0)
+    grid = gpe.gpe_grid_create_dense(case.gbox, ind, 0.0)
+    gpe.gpe_grid_set_potential(grid, 0, case.V)
+    gpe.gpe_grid_set_potential(grid, 1, case.V1)
+    st = gpe.gpe_state_create(grid, gpe.GPE_C128)
+    try:
+        gpe.gpe_state_load(st, np.ascontiguousarray(case.psi), gpe.GPE_LAYOUT_DENSE)
+        gpe.gpe_state_set_graph(st, 5)
+        side = torch.cuda.Stream()
+        p = gpe.real_params(case.g, case.dt, gpe.GPE_V_BLEND, case.knots, case.T)
+        t0 = 3 * case.dt
+        with torch.cuda.stream(side):
+            gpe.gpe_step_real(st, p, 12, t0, stream=side)
+        torch.cuda.synchronize()
+        og = oracle.Grid(case.region, case.box.hx)
+        y = og.compact(case.psi)
+        for q in range(12):
+            y = oracle.rk4_step(og, og.compact(case.V), y, case.g, t0 + q * case.dt, case.dt,
+                                og.compact(case.V1), case.knots, case.T)
+        out = np.zeros(case.box.shape, np.complex128)
+        gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_DENSE)
+        assert rel_l2(out, og.dense(y)) <= 1e-12
+    finally:
+        gpe.gpe_state_destroy(st)
+        gpe.gpe_grid_destroy(grid)
+
+
+def test_autotune_returns_a_timed_valid_layout():
+    wl = inputs.SHELL_96
+    b = wl.box
+    box = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    best, allr = gpe.gpe_autotune(box, pot, wl.V_cut, gpe.GPE_C64, gpe.GPE_TUNE_REAL, 5)
+    assert len(allr) == 7 and best["cell_steps_per_s"] == max(r["cell_steps_per_s"] for r in allr)
+    assert (best["bx"], best["by"], best["bz"]) in {(8, 8, 8), (8, 8, 4), (8, 4, 4)}
+    cached, none = gpe.gpe_autotune(box, pot, wl.V_cut, gpe.GPE_C64, gpe.GPE_TUNE_REAL, 5, timings=False)
+    assert none == [] and cached == best
+    # the chosen layout builds and steps
+    grid = gpe.gpe_grid_create_analytic(box, pot, wl.V_cut, gpe.make_opts(
+        (best["bx"], best["by"], best["bz"]), sched=best["sched"], chunk=best["chunk"]))
+    st = gpe.gpe_state_create(grid, gpe.GPE_C64)
+    gpe.gpe_step_real(st, gpe.real_params(wl.g, wl.stable_dt()), 2)
+    gpe.gpe_state_destroy(st)
+    gpe.gpe_grid_destroy(grid)
