@@ -350,6 +350,29 @@ int gpe_batch_ground_state(gpe_batch *batch, const gpe_imag_params *per_shell,
 
 int gpe_batch_destroy(gpe_batch *batch);
 
+/* ------------------------------------------------------------------ adjoint */
+/* Ramp gradient by the discrete adjoint of the RK4 step (not in the paper:
+ * its ramps are optimised by a derivative-free search, Sec. V; here the
+ * gradient is exact for the discrete RK4 map).
+ *
+ * gpe_ramp_forward runs nsteps real-time RK4 steps of a GPE_V_BLEND ramp from
+ * the state's psi (as gpe_step_real, from time t0) and records a tape: a
+ * checkpoint of psi every K steps, kept in device memory (ceil(nsteps/K)
+ * copies of the state plus K more for the backward pass).  The state ends at
+ * psi(T).  Asynchronous for the steps; returns the tape.
+ *
+ * gpe_ramp_backward computes L = 1 - |<target|psi(T)>|^2 (target: a state on
+ * the same grid and type, e.g. the ground state of the final potential) and
+ * dL/d knots[k] for k < n_knots, by recomputing each K-step segment from its
+ * checkpoint and applying the transposed RK4 step in reverse (bulk in the
+ * state's precision, gradient accumulated in FP64).  The tape can be reused
+ * with other targets while the state still holds psi(T).  Synchronous. */
+int gpe_ramp_forward(gpe_state *st, const gpe_real_params *p, int64_t nsteps,
+                     double t0, int K, gpe_tape **out, gpe_stream stream);
+int gpe_ramp_backward(gpe_tape *tape, const gpe_state *target,
+                      double *grad_knots, double *loss, gpe_stream stream);
+int gpe_tape_destroy(gpe_tape *tape);
+
 /* ------------------------------------------------------------------ tuning */
 enum { GPE_TUNE_REAL = 0, GPE_TUNE_IMAG = 1 };
 typedef struct gpe_tune_result {

@@ -289,4 +289,104 @@ __device__ __forceinline__ double block_sum(double x)
     return x;
 }
 
+// ------------------------------------------------------------ RK4 stages
+// Memory-optimised RK4 (App. A, RK4 a* and b*): the stage states are stored
+// instead of the k_i, so stage i reads only the state it differentiates (with
+// halo) plus the own-cell values of earlier states:
+//   stage 0: y2 = y0 + dt/2 f(t, y0)
+//   stage 1: y3 = y0 + dt/2 f(t + dt/2, y2)
+//   stage 2: y4 = y0 + dt   f(t + dt/2, y3)
+//   stage 3: y1 = (-y0 + y2 + 2 y3 + y4)/3 + dt/6 f(t + dt, y4)  (in place of y0)
+// with f(t, y) = -i [ -1/2 lap y + (V(t) + g|y|^2) y ]  (Eq. (8)).
+template <typename R>
+struct RkArgs {
+    using CT = typename Cx<R>::T;
+    CT *y0;
+    CT *y2;
+    CT *y3;
+    CT *y4;
+    const R *V0;
+    const R *V1;
+    R ihx2, ihy2, ihz2, g, dt;
+    Ramp ramp;
+    double t_off;  // stage-0 time of this step relative to *ramp.clock
+    double dtd;    // dt in FP64 for stage times
+};
+
+template <typename R, bool BLEND>
+__device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
+{
+    if (!BLEND) return (R)0;
+    const double c = (st == 0) ? 0.0 : (st == 3 ? 1.0 : 0.5);
+    return (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + c * a.dtd);
+}
+
+// One RK4 stage on brick b, one warp, lane = segment within each group of 32.
+template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG>
+__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int st, int64_t b, BrickRec *Rr,
+                                          R s)
+{
+    using S = Seg<BX, BY, BZ>;
+    using CT = typename Cx<R>::T;
+    const CT *yin = st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4;
+    CT *yout = st == 0 ? a.y2 : st == 1 ? a.y3 : st == 2 ? a.y4 : a.y0;
+    const R k = (st == 2) ? a.dt : (st == 3 ? a.dt / (R)6 : a.dt / (R)2);
+    load_recs(Rr, G, b);
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int it = 0; it < S::NIT; ++it) {
+        const int q = it * 32 + lane;
+        uint32_t idx = 0;
+        const bool stored = seg_index(Rr[0], q, idx);
+        R V0[4], V1[4];
+        CT y0[4], y2[4], y3[4];
+        if (stored) {
+            ldr4(a.V0 + idx, V0);
+            if (BLEND) ldr4(a.V1 + idx, V1);
+            if (st > 0) ld4<CG>(a.y0 + idx, y0);
+            if (st == 3) {
+                ld4<CG>(a.y2 + idx, y2);
+                ld4<CG>(a.y3 + idx, y3);
+            }
+        }
+        CT c[4], L[4];
+        gather<BX, BY, BZ, CG>(yin, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
+        if (!stored) continue;
+        CT o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (!(V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
+                o[i] = czero<CT>();
+                continue;
+            }
+            const R V = BLEND ? ((R)1 - s) * V0[i] + s * V1[i] : V0[i];
+            const R w = V + a.g * (c[i].x * c[i].x + c[i].y * c[i].y);
+            const R hr = (R)(-0.5) * L[i].x + w * c[i].x;
+            const R hi = (R)(-0.5) * L[i].y + w * c[i].y;
+            // f = -i (hr + i hi) = hi - i hr
+            if (st == 0) {
+                o[i].x = c[i].x + k * hi;
+                o[i].y = c[i].y - k * hr;
+            } else if (st < 3) {
+                o[i].x = y0[i].x + k * hi;
+                o[i].y = y0[i].y - k * hr;
+            } else {
+                o[i].x = (-y0[i].x + y2[i].x + (R)2 * y3[i].x + c[i].x) / (R)3 + k * hi;
+                o[i].y = (-y0[i].y + y2[i].y + (R)2 * y3[i].y + c[i].y) / (R)3 - k * hr;
+            }
+        }
+        st4(yout + idx, o);
+    }
+}
+
+template <typename R, int BX, int BY, int BZ, bool BLEND>
+__global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G, int st)
+{
+    __shared__ BrickRec s_rec[WARPS][7];
+    const int warp = threadIdx.x >> 5;
+    const R s = stage_s<R, BLEND>(a, st);
+    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
+        rk4_brick<R, BX, BY, BZ, BLEND, false>(a, G, st, b, s_rec[warp], s);
+}
+
 }  // namespace gpe

@@ -145,6 +145,9 @@ _SIGS = {
     "gpe_batch_destroy": (C.c_int, [_P]),
     "gpe_autotune": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.c_double, C.c_int, C.c_int, C.c_int,
                                C.POINTER(gpe_tune_result), C.POINTER(gpe_tune_result), C.POINTER(C.c_int), _P]),
+    "gpe_ramp_forward": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, C.c_int, C.POINTER(_P), _P]),
+    "gpe_ramp_backward": (C.c_int, [_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P]),
+    "gpe_tape_destroy": (C.c_int, [_P]),
     "gpe_overlap_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_double), _P]),
     "gpe_ground_state": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_double, C.c_int64, C.c_int64,
                                    C.POINTER(C.c_int64), C.POINTER(gpe_obs), _P]),
@@ -474,6 +477,25 @@ def gpe_autotune(box, pot, V_cut, dtype, mode, nsteps, timings=True, stream=None
     _check(load().gpe_autotune(C.byref(box), C.byref(pot), float(V_cut), int(dtype), int(mode), int(nsteps),
                                C.byref(best), allr if timings else None, C.byref(n), stream_handle(stream)))
     return best.asdict(), [allr[i].asdict() for i in range(n.value)]
+
+
+def gpe_ramp_forward(state, params: gpe_real_params, nsteps, t0=0.0, K=64, stream=None):
+    out = _P()
+    _check(load().gpe_ramp_forward(state, C.byref(params), int(nsteps), float(t0), int(K), C.byref(out),
+                                   stream_handle(stream)))
+    return out.value
+
+
+def gpe_ramp_backward(tape, target, n_knots, stream=None):
+    """Returns (loss, gradient list of n_knots floats)."""
+    grad = (C.c_double * GPE_MAX_KNOTS)()
+    loss = C.c_double()
+    _check(load().gpe_ramp_backward(tape, target, grad, C.byref(loss), stream_handle(stream)))
+    return loss.value, list(grad)[:n_knots]
+
+
+def gpe_tape_destroy(tape):
+    _check(load().gpe_tape_destroy(tape))
 
 
 def gpe_overlap_noalloc(a, b, n, dtype, dV, stream=None) -> complex:
