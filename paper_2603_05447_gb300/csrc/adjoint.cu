@@ -69,31 +69,21 @@ struct Scale {
 template <typename R, int BX, int BY, int BZ, bool BLEND>
 __global__ void GPE_BOUNDS(R) k_adj_stage(const AdjArgs<R> a, const GridView G)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
-    __shared__ BrickRec s_rec[WARPS][7];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
+    const int warp = threadIdx.x >> 5;
     double dot[1] = {0.0};
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS) {
-        BrickRec *Rr = s_rec[warp];
-        load_recs(Rr, G, b);
-#pragma unroll 1
-        for (int it = 0; it < S::NIT; ++it) {
-            const int q = it * 32 + lane;
-            uint32_t idx = 0;
-            const bool stored = seg_index(Rr[0], q, idx);
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
+        brick_apply<BX, BY, BZ, false>(ws, G, b, a.mu_in, Scale<R>{a.m_scale}, a.ihx2, a.ihy2, a.ihz2,
+                                       [&](uint32_t idx, const CT(&M)[4], const CT(&L)[4]) {
             R V0[4], V1[4];
             CT Y[4], lam[4], acc[4];
-            if (stored) {
-                ldr4(a.V0 + idx, V0);
-                if (BLEND) ldr4(a.V1 + idx, V1);
-                ld4<false>(a.Y + idx, Y);
-                ld4<false>(a.lam + idx, lam);
-                if (!a.first) ld4<false>(a.acc + idx, acc);
-            }
-            CT M[4], L[4];
-            gather<BX, BY, BZ, false>(a.mu_in, Rr, q, stored, idx, Scale<R>{a.m_scale}, a.ihx2, a.ihy2, a.ihz2, M, L);
-            if (!stored) continue;
+            ldr4(a.V0 + idx, V0);
+            if (BLEND) ldr4(a.V1 + idx, V1);
+            ld4<false>(a.Y + idx, Y);
+            ld4<false>(a.lam + idx, lam);
+            if (!a.first) ld4<false>(a.acc + idx, acc);
             CT nacc[4], mo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -128,7 +118,7 @@ __global__ void GPE_BOUNDS(R) k_adj_stage(const AdjArgs<R> a, const GridView G)
                 st4(a.acc + idx, nacc);
                 st4(a.mu_out + idx, mo);
             }
-        }
+        });
     }
     double tot[1];
     if (reduce_finish<1>(dot, a.partials, a.counter, tot) && threadIdx.x == 0 && BLEND) {
@@ -281,15 +271,12 @@ extern "C" int gpe_ramp_forward(gpe_state *st, const gpe_real_params *p, int64_t
 
 namespace gpe {
 
-template <typename K>
-static int adj_blocks(K kernel, const gpe_grid *g)
+template <typename R, typename K>
+static int adj_blocks(K kernel, const gpe_grid *g, size_t smem)
 {
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0) != cudaSuccess || per < 1) {
-        cudaGetLastError();
-        per = 1;
-    }
-    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->nsm * per, (g->nb + WARPS - 1) / WARPS));
+    const int per = prepare_kernel(kernel, KernelCfg<R>::THREADS, smem);
+    const int64_t need = (g->nb + KernelCfg<R>::NW - 1) / KernelCfg<R>::NW;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->nsm * per, need));
 }
 
 template <typename R, int BX, int BY, int BZ>
@@ -330,7 +317,9 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
     for (int k = 0; k < GPE_MAX_KNOTS; ++k) f.ramp.knots[k] = p.knots[k];
     auto kf = k_rk4_staged<R, BX, BY, BZ, true>;
     auto ka = k_adj_stage<R, BX, BY, BZ, true>;
-    const int nbf = adj_blocks(kf, g), nba = adj_blocks(ka, g);
+    const size_t smem = smem_bytes<R, BX, BY, BZ>();
+    const int th = KernelCfg<R>::THREADS;
+    const int nbf = adj_blocks<R>(kf, g, smem), nba = adj_blocks<R>(ka, g, smem);
     AdjArgs<R> a{};
     a.lam = lam;
     a.lam_out = lam;
@@ -355,7 +344,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
             f.y0 = seg + (m + 1) * np;
             f.t_off = t->t0 + (double)(j * t->K + m) * p.dt;
             for (int stg = 0; stg < 4; ++stg) {
-                kf<<<nbf, 256, 0, s>>>(f, G, stg);
+                kf<<<nbf, th, smem, s>>>(f, G, stg);
                 GPE_LAUNCH_CHECK();
             }
         }
@@ -364,7 +353,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
             f.y0 = seg + m * np;
             f.t_off = tm;
             for (int stg = 0; stg < 3; ++stg) {  // Y2, Y3, Y4
-                kf<<<nbf, 256, 0, s>>>(f, G, stg);
+                kf<<<nbf, th, smem, s>>>(f, G, stg);
                 GPE_LAUNCH_CHECK();
             }
             // stages 4, 3, 2, 1 of the reverse sweep
@@ -384,7 +373,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
                 a.first = r == 0;
                 a.last = r == 3;
                 hat(p, ts[r], a.k0, a.w0, a.w1);
-                ka<<<nba, 256, 0, s>>>(a, G);
+                ka<<<nba, th, smem, s>>>(a, G);
                 GPE_LAUNCH_CHECK();
             }
         }

@@ -51,35 +51,20 @@ __device__ __forceinline__ int shell_of(const BrickRec &r) { return (int)r.pad[0
 template <typename R, int BX, int BY, int BZ, int STAGE>
 __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS) {
-        BrickRec *Rr = s_rec[warp];
-        load_recs(Rr, G, b);
-        const int s = shell_of(Rr[0]);
-        const ShellParams &P = a.sh[s];
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
+        const ShellParams &P = a.sh[shell_of(G.rec[b])];
         if (P.converged) continue;  // uniform across the warp
         const R g = (R)P.g, dt = (R)P.dt;
         const R ihx2 = (R)P.ihx2, ihy2 = (R)P.ihy2, ihz2 = (R)P.ihz2;
         const R q4 = dt / (R)4, hg = g * dt / (R)2;
         double acc = 0.0;
-#pragma unroll 1
-        for (int it = 0; it < S::NIT; ++it) {
-            const int q = it * 32 + lane;
-            uint32_t idx = 0;
-            const bool stored = seg_index(Rr[0], q, idx);
+        auto body = [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
             R E[4];
-            if (stored) ldr4(a.E + idx, E);
-            CT c[4], L[4];
-            if (STAGE == 0) {
-                const DiagLoad<R> diag{(R)P.scale, hg, a.E};
-                gather<BX, BY, BZ, false>(a.psi, Rr, q, stored, idx, diag, ihx2, ihy2, ihz2, c, L);
-            } else {
-                gather<BX, BY, BZ, false>(a.tmp, Rr, q, stored, idx, Identity(), ihx2, ihy2, ihz2, c, L);
-            }
-            if (!stored) continue;
+            ldr4(a.E + idx, E);
             CT o[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -96,7 +81,11 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G
                 }
             }
             st4((STAGE == 0 ? a.tmp : a.psi) + idx, o);
-        }
+        };
+        if (STAGE == 0)
+            brick_apply<BX, BY, BZ, false>(ws, G, b, a.psi, DiagLoad<R>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2, body);
+        else
+            brick_apply<BX, BY, BZ, false>(ws, G, b, a.tmp, Identity(), ihx2, ihy2, ihz2, body);
         if (STAGE == 1) {
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
             if (lane == 0) a.part[b * 5] = acc;
@@ -148,28 +137,19 @@ __global__ void k_batch_reset_scale(ShellParams *sh, int n)
 template <typename R, int BX, int BY, int BZ>
 __global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R> a, const GridView G)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS) {
-        BrickRec *Rr = s_rec[warp];
-        load_recs(Rr, G, b);
-        const ShellParams &P = a.sh[shell_of(Rr[0])];
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
+        const ShellParams &P = a.sh[shell_of(G.rec[b])];
         if (P.converged) continue;
         const R g = (R)P.g;
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll 1
-        for (int it = 0; it < S::NIT; ++it) {
-            const int q = it * 32 + lane;
-            uint32_t idx = 0;
-            const bool stored = seg_index(Rr[0], q, idx);
+        brick_apply<BX, BY, BZ, false>(ws, G, b, a.psi, Identity(), (R)P.ihx2, (R)P.ihy2, (R)P.ihz2,
+                                       [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
             R V[4];
-            if (stored) ldr4(a.V + idx, V);
-            CT c[4], L[4];
-            gather<BX, BY, BZ, false>(a.psi, Rr, q, stored, idx, Identity(), (R)P.ihx2, (R)P.ihy2, (R)P.ihz2, c,
-                                      L);
-            if (!stored) continue;
+            ldr4(a.V + idx, V);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!(V[i] < (R)INFINITY)) continue;
@@ -180,7 +160,7 @@ __global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R> a, const GridView G
                 acc[3] += (double)((R)0.5 * g * rho * rho);
                 acc[4] += (isfinite(c[i].x) && isfinite(c[i].y)) ? 0.0 : 1.0;
             }
-        }
+        });
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             double x = acc[k];
@@ -257,6 +237,7 @@ struct gpe_batch {
     int64_t nb = 0, np = 0;
     int32_t *d_nbr = nullptr;
     BrickRec *d_rec = nullptr;
+    BrickRec *d_rec7 = nullptr;
     void *d_psi = nullptr, *d_tmp = nullptr, *d_E = nullptr, *d_Vr = nullptr;
     double *d_V = nullptr;
     ShellParams *d_sh = nullptr;
@@ -276,6 +257,7 @@ static void batch_free(gpe_batch *B)
     if (B->cap) cudaStreamDestroy(B->cap);
     dev_free(B->d_nbr);
     dev_free(B->d_rec);
+    dev_free(B->d_rec7);
     dev_free(B->d_psi);
     dev_free(B->d_tmp);
     dev_free(B->d_E);
@@ -328,6 +310,7 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
     if (B->np >= 0xffffffffLL) BT(fail(GPE_ERR_ARG, "batch too large for 32-bit packed offsets"));
     BT(dev_alloc_t(&B->d_nbr, B->nb * 6));
     BT(dev_alloc_t(&B->d_rec, B->nb));
+    BT(dev_alloc_t(&B->d_rec7, B->nb * 7));
     BT(dev_alloc(&B->d_psi, B->np * B->elem));
     BT(dev_alloc(&B->d_tmp, B->np * B->elem));
     BT(dev_alloc(&B->d_E, B->np * B->elem / 2));
@@ -357,6 +340,10 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
             cudaSuccess)
             BT(fail(GPE_ERR_CUDA, "batch potential copy failed"));
     }
+    std::vector<BrickRec> rec7;
+    build_rec7(rec, nbr, rec7);
+    if (cudaMemcpy(B->d_rec7, rec7.data(), rec7.size() * sizeof(BrickRec), cudaMemcpyHostToDevice) != cudaSuccess)
+        BT(fail(GPE_ERR_CUDA, "batch table upload failed"));
     if (cudaMemcpy(B->d_nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(B->d_rec, rec.data(), rec.size() * sizeof(BrickRec), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(B->d_bb, B->brick_base.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -396,21 +383,19 @@ static int batch_record_block(gpe_batch *B, int64_t nsteps, cudaStream_t s)
     a.part = B->d_part;
     a.brick_base = B->d_bb;
     a.n = B->n;
-    const GridView G{B->d_nbr, B->d_rec, B->nb};
+    const GridView G{B->d_nbr, B->d_rec, B->d_rec7, B->nb};
     auto ka = k_batch_itp<R, BX, BY, BZ, 0>;
     auto kb = k_batch_itp<R, BX, BY, BZ, 1>;
     auto ko = k_batch_obs<R, BX, BY, BZ>;
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ka, 256, 0) != cudaSuccess || per < 1) {
-        cudaGetLastError();
-        per = 1;
-    }
-    const int64_t need = (B->nb + WARPS - 1) / WARPS;
+    const int th = KernelCfg<R>::THREADS;
+    const size_t smem = smem_bytes<R, BX, BY, BZ>();
+    const int per = std::min(prepare_kernel(ka, th, smem), std::min(prepare_kernel(kb, th, smem), prepare_kernel(ko, th, smem)));
+    const int64_t need = (B->nb + KernelCfg<R>::NW - 1) / KernelCfg<R>::NW;
     const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->nsm * per, need));
     for (int64_t k = 0; k < nsteps; ++k) {
-        ka<<<nblk, 256, 0, s>>>(a, G);
+        ka<<<nblk, th, smem, s>>>(a, G);
         GPE_LAUNCH_CHECK();
-        kb<<<nblk, 256, 0, s>>>(a, G);
+        kb<<<nblk, th, smem, s>>>(a, G);
         GPE_LAUNCH_CHECK();
         k_batch_norm_finish<<<B->n, 256, 0, s>>>(B->d_sh, B->d_part, B->d_bb);
         GPE_LAUNCH_CHECK();
@@ -422,7 +407,7 @@ static int batch_record_block(gpe_batch *B, int64_t nsteps, cudaStream_t s)
     GPE_LAUNCH_CHECK();
     k_zero_int<<<1, 1, 0, s>>>(B->d_unconv);
     GPE_LAUNCH_CHECK();
-    ko<<<nblk, 256, 0, s>>>(a, G);
+    ko<<<nblk, th, smem, s>>>(a, G);
     GPE_LAUNCH_CHECK();
     k_batch_obs_finish<<<B->n, 256, 0, s>>>(B->d_sh, B->d_part, B->d_bb, B->d_unconv);
     GPE_LAUNCH_CHECK();

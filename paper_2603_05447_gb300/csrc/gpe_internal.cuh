@@ -22,6 +22,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "gpe.h"
 
@@ -74,6 +75,10 @@ struct BrickRec {
     uint32_t pre;   // byte w: stored segments in mask words < w
     uint32_t pad[2];
 };
+
+// per brick: its record followed by its six face neighbours' (-x +x -y +y -z
+// +z; empty records for absent neighbours), built on the host
+void build_rec7(const std::vector<BrickRec> &rec, const std::vector<int32_t> &nbr, std::vector<BrickRec> &out);
 
 // packed index of the first cell of segment q, if stored
 __host__ __device__ __forceinline__ bool seg_index(const BrickRec &r, int q, uint32_t &idx)
@@ -289,6 +294,7 @@ struct gpe_grid {
     int32_t *d_nbr = nullptr;
     uint32_t *d_mask = nullptr;
     gpe::BrickRec *d_rec = nullptr;
+    gpe::BrickRec *d_rec7 = nullptr;  // [nb*7] record of each brick and of its six face neighbours
     int32_t *d_bvol = nullptr;  // brick-grid volume nbx*nby*nbz -> brick id or -1
     double *d_V[2] = {nullptr, nullptr};
     float *d_Vf[2] = {nullptr, nullptr};  // float copies, made on first use

@@ -329,6 +329,21 @@ __global__ void k_vmax(int64_t np, const double *V0, const double *V1, unsigned 
     if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(vm));
 }
 
+}  // namespace gpe
+
+void gpe::build_rec7(const std::vector<BrickRec> &rec, const std::vector<int32_t> &nbr, std::vector<BrickRec> &out)
+{
+    const size_t nb = rec.size();
+    out.assign(nb * 7, BrickRec{});
+    for (size_t b = 0; b < nb; ++b) {
+        out[7 * b] = rec[b];
+        for (int d = 0; d < 6; ++d)
+            if (nbr[6 * b + d] >= 0) out[7 * b + 1 + d] = rec[nbr[6 * b + d]];
+    }
+}
+
+namespace gpe {
+
 static BoxD boxd(const gpe_box &b)
 {
     return BoxD{b.nx, b.ny, b.nz, b.hx, b.hy, b.hz, b.x0, b.y0, b.z0};
@@ -369,6 +384,7 @@ static void grid_free(gpe_grid *g)
 {
     if (!g) return;
     dev_free(g->d_rec);
+    dev_free(g->d_rec7);
     dev_free(g->d_chunk_lohi);
     dev_free(g->d_tasks);
     dev_free(g->d_org);
@@ -556,6 +572,16 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     }
     g->n_packed = (int64_t)acc;
     BUILD_CUDA(cudaMemcpyAsync(g->d_rec, hrec.data(), total * sizeof(BrickRec), cudaMemcpyHostToDevice, st));
+    {
+        std::vector<int32_t> hnbr(total * 6);
+        BUILD_CUDA(cudaMemcpyAsync(hnbr.data(), g->d_nbr, total * 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaStreamSynchronize(st));
+        std::vector<BrickRec> h7;
+        build_rec7(hrec, hnbr, h7);
+        BUILD_TRY(dev_alloc_t(&g->d_rec7, total * 7));
+        BUILD_CUDA(cudaMemcpyAsync(g->d_rec7, h7.data(), h7.size() * sizeof(BrickRec), cudaMemcpyHostToDevice, st));
+        BUILD_CUDA(cudaStreamSynchronize(st));
+    }
     for (int sl = 0; sl < g->n_slots; ++sl) {
         BUILD_TRY(dev_alloc_t(&g->d_V[sl], g->n_packed));
         k_pack<<<g->nsm * 8, 256, 0, st>>>(g->n_stored, g->bc, g->d_mask, g->d_rec, tmpV[sl], g->d_V[sl],

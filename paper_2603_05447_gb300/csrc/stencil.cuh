@@ -1,6 +1,6 @@
 // stencil.cuh -- device building blocks shared by the stencil kernels of
 // libgpeshell (steps, batches, adjoint): the packed segment layout, the
-// warp-per-brick gather of a segment's 7-point Laplacian (Eq. (B1)), the ramp
+// per-warp brick tile and its 7-point Laplacian (Eq. (B1)), the ramp
 // schedule and small reductions.  Not part of the ABI.
 #pragma once
 
@@ -8,18 +8,23 @@
 
 namespace gpe {
 
-// The warps of a block share the per-warp record slots below.
-constexpr int WARPS = 8;  // blocks of 256 threads, one brick per warp at a time
+// Stencil kernels run one brick per warp; a block holds NW warps, each with
+// its own shared-memory workspace (brick tile with face halo, the 7 brick
+// records and the list of stored segments), passed as dynamic shared memory.
+template <typename R>
+struct KernelCfg {
+    static constexpr int NW = sizeof(R) == 4 ? 8 : 4;  // warps per block
+    static constexpr int THREADS = 32 * NW;
+};
 
-// Minimum resident blocks per SM requested from the register allocator for
-// the stencil kernels (complex64 / complex128 bulk).
+// Minimum resident blocks per SM requested from the register allocator.
 #ifndef GPE_MINB_F
-#define GPE_MINB_F 2
+#define GPE_MINB_F 3
 #endif
 #ifndef GPE_MINB_D
-#define GPE_MINB_D 1
+#define GPE_MINB_D 3
 #endif
-#define GPE_BOUNDS(R) __launch_bounds__(256, (sizeof(R) == 4 ? GPE_MINB_F : GPE_MINB_D))
+#define GPE_BOUNDS(R) __launch_bounds__(KernelCfg<R>::THREADS, (sizeof(R) == 4 ? GPE_MINB_F : GPE_MINB_D))
 
 // ------------------------------------------------------------ packed layout
 // supported brick shapes (shape id, BX, BY, BZ)
@@ -31,10 +36,11 @@ constexpr int WARPS = 8;  // blocks of 256 threads, one brick per warp at a time
 struct GridView {
     const int32_t *nbr;
     const BrickRec *rec;
+    const BrickRec *rec7;  // per brick: its record, then its six face neighbours' (empty if absent)
     int64_t nb;
 };
 
-inline GridView view(const gpe_grid *g) { return GridView{g->d_nbr, g->d_rec, g->nb}; }
+inline GridView view(const gpe_grid *g) { return GridView{g->d_nbr, g->d_rec, g->d_rec7, g->nb}; }
 
 // segment geometry of a brick shape (BX must be 8: two segments per row)
 template <int BX, int BY, int BZ>
@@ -145,93 +151,199 @@ struct Identity {
 };
 
 // Records of brick b (slot 0) and of its six face neighbours (slots 1..6,
-// order -x +x -y +y -z +z; an absent neighbour gets an empty record), loaded by
-// one warp into its shared-memory slots.
+// order -x +x -y +y -z +z; an absent neighbour has an empty record): one
+// coalesced 224-byte load by 14 lanes into the warp's shared-memory slots.
 __device__ __forceinline__ void load_recs(BrickRec *R, const GridView &G, int64_t b)
 {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    if (lane < 7) {
-        const int64_t id = lane == 0 ? b : (int64_t)__ldg(&G.nbr[b * 6 + lane - 1]);
-        uint4 a = make_uint4(0, 0, 0, 0), c = make_uint4(0, 0, 0, 0);
-        if (id >= 0) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(G.rec + id);
-            a = __ldg(p);
-            c = __ldg(p + 1);
-        }
-        uint4 *d = reinterpret_cast<uint4 *>(R + lane);
-        d[0] = a;
-        d[1] = c;
-    }
+    if (lane < 14) reinterpret_cast<uint4 *>(R)[lane] = __ldg(reinterpret_cast<const uint4 *>(G.rec7 + 7 * b) + lane);
     __syncwarp();
 }
 
-// One lane's segment q of a brick: its four values c[] and their 7-point
-// Laplacians L[] (Eq. (B1)), every loaded value passed through xf first.
-// All 32 lanes must call this together: x and y neighbours inside the brick
-// come from other lanes by shuffles; z neighbours and brick-boundary
-// neighbours are loaded.  Every load of the lane is issued before the first
-// shuffle so that they are in flight together.
 template <bool CG, typename CT>
 __device__ __forceinline__ CT ld1(const CT *p)
 {
     return CG ? __ldcg(p) : *p;
 }
 
-template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF>
-__device__ __forceinline__ void gather(const CT *src, const BrickRec *Rr, int q, bool stored, uint32_t idx, XF xf,
-                                       R ihx2, R ihy2, R ihz2, CT (&c)[4], CT (&L)[4])
+// Per-warp workspace: the brick's cells with the y and z face halos as whole
+// rows (BX cells per row, rows y = -1..BY, planes z = -1..BZ), the x face
+// halos as separate columns (so every row, and every segment, starts on a
+// 16-byte boundary for vector shared-memory access), the records of the brick
+// and its six face neighbours, and the brick's stored segments in order.
+template <typename CT, int BX, int BY, int BZ>
+struct WarpSpace {
+    static constexpr int TY = BY + 2, TZ = BZ + 2;
+    static constexpr int NSEG = Seg<BX, BY, BZ>::NSEG;
+    static constexpr int ROW = BX, PLANE = BX * TY;
+    __device__ __forceinline__ static int m(int x, int y, int z) { return x + BX * ((y + 1) + TY * (z + 1)); }
+    __device__ __forceinline__ static int h(int y, int z) { return y + BY * z; }
+    CT main[BX * TY * TZ];
+    CT xlo[BY * BZ];  // x = -1
+    CT xhi[BY * BZ];  // x = BX
+    BrickRec rec[7];
+    uint8_t list[NSEG];
+    uint8_t pad[(16 - (NSEG % 16)) % 16];
+};
+
+// 4 complex values to / from shared memory at a 16-byte aligned address
+__device__ __forceinline__ void sget4(const float2 *p, float2 (&v)[4])
+{
+    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void sget4(const double2 *p, double2 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = p[i];
+}
+__device__ __forceinline__ void sput4(float2 *p, const float2 (&v)[4])
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+__device__ __forceinline__ void sput4(double2 *p, const double2 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = v[i];
+}
+
+template <typename R, int BX, int BY, int BZ>
+constexpr size_t smem_bytes()
+{
+    return (size_t)KernelCfg<R>::NW * sizeof(WarpSpace<typename Cx<R>::T, BX, BY, BZ>);
+}
+
+template <typename R, int BX, int BY, int BZ>
+__device__ __forceinline__ WarpSpace<typename Cx<R>::T, BX, BY, BZ> &warp_space()
+{
+    extern __shared__ __align__(16) unsigned char gpe_smem[];
+    return reinterpret_cast<WarpSpace<typename Cx<R>::T, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
+}
+
+template <typename CT>
+__device__ __forceinline__ void put4(CT *t, const CT (&v)[4])
+{
+    t[0] = v[0];
+    t[1] = v[1];
+    t[2] = v[2];
+    t[3] = v[3];
+}
+
+// Apply body(idx, c, L) to every stored segment of brick b, one warp: idx is
+// the packed index of the segment's first cell, c[4] its values and L[4]
+// their 7-point Laplacians (Eq. (B1)), all taken from src after xf(value,
+// packed index).  The warp first stages the brick's stored segments (32-byte
+// vector loads, coalesced along the packed run) and the face halos from the
+// neighbour bricks into its tile; absent cells read as zero.  Lanes then take
+// the stored segments in order, so the packed indices of a warp's segments
+// are consecutive and the bodies' own-cell loads and stores coalesce.
+template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename BODY>
+__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b,
+                                            const CT *src, XF xf, R ihx2, R ihy2, R ihz2, BODY body)
 {
     using S = Seg<BX, BY, BZ>;
-    const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-    // neighbour segments that live in memory
-    uint32_t jzm = 0, jzp = 0, jy = 0, jx = 0;
-    const bool hzm = stored && (z == 0 ? seg_index(Rr[5], q + S::PLANE * (BZ - 1), jzm)
-                                       : seg_index(Rr[0], q - S::PLANE, jzm));
-    const bool hzp = stored && (z == BZ - 1 ? seg_index(Rr[6], q - S::PLANE * (BZ - 1), jzp)
-                                            : seg_index(Rr[0], q + S::PLANE, jzp));
-    const bool ylo = (y == 0), yhi = (y == BY - 1);
-    const bool hy = stored && (ylo ? seg_index(Rr[3], hx + S::SX * (BY - 1) + S::PLANE * z, jy)
-                                   : (yhi && seg_index(Rr[4], hx + S::PLANE * z, jy)));
-    // x: segment (1, y, z) of the -x brick (cell x = 7) or (0, y, z) of the +x brick (cell x = 0)
-    const bool hxb = stored && (hx == 0 ? seg_index(Rr[1], q + 1, jx) : seg_index(Rr[2], q - 1, jx));
-    if (hx == 0) jx += 3;
-    CT zm[4], zp[4], yb[4], xb = czero<CT>();
+    using W = WarpSpace<CT, BX, BY, BZ>;
+    const int lane = threadIdx.x & 31;
+    load_recs(ws.rec, G, b);
+    const BrickRec &R0 = ws.rec[0];
+    auto seg4 = [&](const BrickRec &r, int q, CT(&v)[4]) {
+        uint32_t j;
+        if (seg_index(r, q, j)) {
+            ld4<CG>(src + j, v);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] = zm[i] = zp[i] = yb[i] = czero<CT>();
-    if (stored) ld4<CG>(src + idx, c);
-    if (hzm) ld4<CG>(src + jzm, zm);
-    if (hzp) ld4<CG>(src + jzp, zp);
-    if (hy) ld4<CG>(src + jy, yb);
-    if (hxb) xb = ld1<CG>(src + jx);
+            for (int i = 0; i < 4; ++i) v[i] = xf(v[i], j + i);
+        } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (stored) c[i] = xf(c[i], idx + i);
-        if (hzm) zm[i] = xf(zm[i], jzm + i);
-        if (hzp) zp[i] = xf(zp[i], jzp + i);
-        if (hy) yb[i] = xf(yb[i], jy + i);
+            for (int i = 0; i < 4; ++i) v[i] = czero<CT>();
+        }
+    };
+    // interior: stored segments from the packed run, zeros elsewhere
+    int nst = 0;
+#pragma unroll
+    for (int it = 0; it < S::NIT; ++it) {
+        const int q = it * 32 + lane;
+        CT v[4];
+        seg4(R0, q, v);
+        const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
+        sput4(ws.main + W::m(4 * hx, y, z), v);
+        const bool stored = (R0.m[q >> 5] >> (q & 31)) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, stored);
+        if (stored) ws.list[nst + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
+        nst += __popc(bal);
     }
-    if (hxb) xb = xf(xb, jx);
-    CT ym[4], yp[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        ym[i] = shfl_up(c[i], S::SX);
-        yp[i] = shfl_down(c[i], S::SX);
-        if (ylo) ym[i] = yb[i];
-        if (yhi) yp[i] = yb[i];
+    // -z / +z faces: whole segments of the neighbours' boundary planes
+    for (int u = lane; u < 2 * S::PLANE; u += 32) {
+        const int face = u / S::PLANE, qc = u % S::PLANE;
+        CT v[4];
+        seg4(ws.rec[5 + face], face == 0 ? qc + S::PLANE * (BZ - 1) : qc, v);
+        sput4(ws.main + W::m(4 * (qc % S::SX), qc / S::SX, face == 0 ? -1 : BZ), v);
     }
-    const CT p0 = shfl_xor(c[0], 1), p3 = shfl_xor(c[3], 1);
-    const CT xm = hx == 0 ? xb : p3;  // left of cell 0
-    const CT xp = hx == 0 ? p0 : xb;  // right of cell 3
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const CT l = i == 0 ? xm : c[i - 1];
-        const CT r = i == 3 ? xp : c[i + 1];
-        L[i].x = (r.x - 2 * c[i].x + l.x) * ihx2 + (yp[i].x - 2 * c[i].x + ym[i].x) * ihy2 +
-                 (zp[i].x - 2 * c[i].x + zm[i].x) * ihz2;
-        L[i].y = (r.y - 2 * c[i].y + l.y) * ihx2 + (yp[i].y - 2 * c[i].y + ym[i].y) * ihy2 +
-                 (zp[i].y - 2 * c[i].y + zm[i].y) * ihz2;
+    // -y / +y faces: segments of the neighbours' boundary rows
+    for (int u = lane; u < 2 * S::SX * BZ; u += 32) {
+        const int face = u / (S::SX * BZ), v_ = u % (S::SX * BZ);
+        const int hx = v_ % S::SX, z = v_ / S::SX;
+        CT v[4];
+        seg4(ws.rec[3 + face], hx + S::SX * (face == 0 ? BY - 1 : 0) + S::PLANE * z, v);
+        sput4(ws.main + W::m(4 * hx, face == 0 ? -1 : BY, z), v);
     }
+    // -x / +x faces: single cells (x = BX-1 of the -x brick, x = 0 of the +x brick)
+    for (int u = lane; u < 2 * BY * BZ; u += 32) {
+        const int face = u / (BY * BZ), v_ = u % (BY * BZ);
+        const int y = v_ % BY, z = v_ / BY;
+        const int q = (face == 0 ? S::SX - 1 : 0) + S::SX * y + S::PLANE * z;
+        uint32_t j;
+        CT v = czero<CT>();
+        if (seg_index(ws.rec[1 + face], q, j)) {
+            j += face == 0 ? 3 : 0;
+            v = xf(ld1<CG>(src + j), j);
+        }
+        (face == 0 ? ws.xlo : ws.xhi)[W::h(y, z)] = v;
+    }
+    __syncwarp();
+    // stored segments: Laplacian from the tile, then the body
+    for (int r = lane; r < nst; r += 32) {
+        const int q = ws.list[r];
+        const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
+        const int base = W::m(4 * hx, y, z);
+        CT c[4], ym[4], yp[4], zm[4], zp[4], L[4];
+        sget4(ws.main + base, c);
+        sget4(ws.main + base - W::ROW, ym);
+        sget4(ws.main + base + W::ROW, yp);
+        sget4(ws.main + base - W::PLANE, zm);
+        sget4(ws.main + base + W::PLANE, zp);
+        const CT xm = hx == 0 ? ws.xlo[W::h(y, z)] : ws.main[base - 1];
+        const CT xp = hx == S::SX - 1 ? ws.xhi[W::h(y, z)] : ws.main[base + 4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const CT l = i == 0 ? xm : c[i - 1];
+            const CT rr = i == 3 ? xp : c[i + 1];
+            L[i].x = (rr.x - 2 * c[i].x + l.x) * ihx2 + (yp[i].x - 2 * c[i].x + ym[i].x) * ihy2 +
+                     (zp[i].x - 2 * c[i].x + zm[i].x) * ihz2;
+            L[i].y = (rr.y - 2 * c[i].y + l.y) * ihx2 + (yp[i].y - 2 * c[i].y + ym[i].y) * ihy2 +
+                     (zp[i].y - 2 * c[i].y + zm[i].y) * ihz2;
+        }
+        body(R0.off + 4u * (uint32_t)r, c, L);
+    }
+}
+
+// one-time launch preparation of a stencil kernel: dynamic shared memory
+// beyond 48 KiB needs an opt-in; returns resident blocks per SM
+template <typename K>
+inline int prepare_kernel(K kernel, int threads, size_t smem)
+{
+    static_assert(sizeof(K) > 0, "");
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    return per;
 }
 
 // ------------------------------------------------------------ ramp schedule
@@ -323,35 +435,24 @@ __device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
 
 // One RK4 stage on brick b, one warp, lane = segment within each group of 32.
 template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG>
-__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int st, int64_t b, BrickRec *Rr,
-                                          R s)
+__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int st, int64_t b,
+                                          WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R s)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
     const CT *yin = st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4;
     CT *yout = st == 0 ? a.y2 : st == 1 ? a.y3 : st == 2 ? a.y4 : a.y0;
     const R k = (st == 2) ? a.dt : (st == 3 ? a.dt / (R)6 : a.dt / (R)2);
-    load_recs(Rr, G, b);
-    const int lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int it = 0; it < S::NIT; ++it) {
-        const int q = it * 32 + lane;
-        uint32_t idx = 0;
-        const bool stored = seg_index(Rr[0], q, idx);
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, yin, Identity(), a.ihx2, a.ihy2, a.ihz2,
+                                [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
         R V0[4], V1[4];
         CT y0[4], y2[4], y3[4];
-        if (stored) {
-            ldr4(a.V0 + idx, V0);
-            if (BLEND) ldr4(a.V1 + idx, V1);
-            if (st > 0) ld4<CG>(a.y0 + idx, y0);
-            if (st == 3) {
-                ld4<CG>(a.y2 + idx, y2);
-                ld4<CG>(a.y3 + idx, y3);
-            }
+        ldr4(a.V0 + idx, V0);
+        if (BLEND) ldr4(a.V1 + idx, V1);
+        if (st > 0) ld4<CG>(a.y0 + idx, y0);
+        if (st == 3) {
+            ld4<CG>(a.y2 + idx, y2);
+            ld4<CG>(a.y3 + idx, y3);
         }
-        CT c[4], L[4];
-        gather<BX, BY, BZ, CG>(yin, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
-        if (!stored) continue;
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -376,17 +477,18 @@ __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G,
             }
         }
         st4(yout + idx, o);
-    }
+    });
 }
 
 template <typename R, int BX, int BY, int BZ, bool BLEND>
 __global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G, int st)
 {
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     const R s = stage_s<R, BLEND>(a, st);
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
-        rk4_brick<R, BX, BY, BZ, BLEND, false>(a, G, st, b, s_rec[warp], s);
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
+        rk4_brick<R, BX, BY, BZ, BLEND, false>(a, G, st, b, ws, s);
 }
 
 }  // namespace gpe

@@ -64,38 +64,33 @@ __global__ void k_make_E(const double *V, R *E, int64_t n, double dt)
 static std::mutex g_occ_mu;
 static std::unordered_map<const void *, int> g_occ;
 
+// resident blocks per SM of a stencil kernel (prepared once: dynamic shared
+// memory opt-in and occupancy query)
 template <typename K>
-static int per_sm_for(K kernel, int threads)
+static int per_sm_for(K kernel, int threads, size_t smem)
 {
     {
         std::lock_guard<std::mutex> lk(g_occ_mu);
         auto it = g_occ.find((const void *)kernel);
         if (it != g_occ.end()) return it->second;
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
+    const int per = prepare_kernel(kernel, threads, smem);
     std::lock_guard<std::mutex> lk(g_occ_mu);
-    g_occ[(const void *)kernel] = per_sm;
-    return per_sm;
+    g_occ[(const void *)kernel] = per;
+    return per;
 }
 
-// every brick kernel runs blocks of 256 threads, one brick per warp
-template <typename K>
-static int blocks_for(K kernel, const gpe_grid *g, int threads)
+// a grid of resident blocks, no more than one warp per brick
+template <typename R, typename K>
+static int blocks_for(K kernel, const gpe_grid *g, size_t smem)
 {
-    int64_t b = (int64_t)g->nsm * per_sm_for(kernel, threads);
-    const int64_t need = (g->nb + 7) / 8;
+    constexpr int NW = KernelCfg<R>::NW;
+    int64_t b = (int64_t)g->nsm * per_sm_for(kernel, KernelCfg<R>::THREADS, smem);
+    const int64_t need = (g->nb + NW - 1) / NW;
     if (b > need) b = need;
     if (b < 1) b = 1;
     return (int)b;
 }
-
-static inline int brick_threads(const gpe_grid *) { return 256; }
-
-
 
 // ------------------------------------------------------------ wavefront sync
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
@@ -193,7 +188,8 @@ template <typename R, int BX, int BY, int BZ, bool BLEND>
 __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, const Wave w)
 {
     using CT = typename Cx<R>::T;
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     R s[4];
 #pragma unroll
@@ -205,7 +201,7 @@ __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, co
         wait_for(w, st, c);
         const int64_t b0 = (int64_t)c * w.cb;
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
-        for (int64_t b = b0 + warp; b < b1; b += WARPS) rk4_brick<R, BX, BY, BZ, BLEND, true>(a, G, st, b, s_rec[warp], s[st]);
+        for (int64_t b = b0 + warp; b < b1; b += NW) rk4_brick<R, BX, BY, BZ, BLEND, true>(a, G, st, b, ws, s[st]);
         publish(w, st, c);
         if (st == 3) {
             // y2 and y3 of this chunk have no reader left in this step
@@ -239,24 +235,16 @@ struct ItpArgs {
 };
 
 template <typename R, int BX, int BY, int BZ, bool CG>
-__device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b, BrickRec *Rr, R sc)
+__device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b,
+                                            WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R sc)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
     const R q4 = a.dt / (R)4;
     const DiagLoad<R> diag{sc, a.g * a.dt / (R)2, a.E};
-    load_recs(Rr, G, b);
-    const int lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int it = 0; it < S::NIT; ++it) {
-        const int q = it * 32 + lane;
-        uint32_t idx = 0;
-        const bool stored = seg_index(Rr[0], q, idx);
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, a.psi, diag, a.ihx2, a.ihy2, a.ihz2,
+                                [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
         R E[4];
-        if (stored) ldr4(a.E + idx, E);
-        CT c[4], L[4];
-        gather<BX, BY, BZ, CG>(a.psi, Rr, q, stored, idx, diag, a.ihx2, a.ihy2, a.ihz2, c, L);
-        if (!stored) continue;
+        ldr4(a.E + idx, E);
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -265,29 +253,20 @@ __device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView 
             o[i].y = act ? c[i].y + q4 * L[i].y : (R)0;
         }
         st4(a.tmp + idx, o);
-    }
+    });
 }
 
 template <typename R, int BX, int BY, int BZ, bool CG>
-__device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView &G, int64_t b, BrickRec *Rr,
-                                            double &acc)
+__device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView &G, int64_t b,
+                                            WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, double &acc)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
     const R hg = a.g * a.dt / (R)2;
     const R q4 = a.dt / (R)4;
-    load_recs(Rr, G, b);
-    const int lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int it = 0; it < S::NIT; ++it) {
-        const int q = it * 32 + lane;
-        uint32_t idx = 0;
-        const bool stored = seg_index(Rr[0], q, idx);
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2,
+                                [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
         R E[4];
-        if (stored) ldr4(a.E + idx, E);
-        CT c[4], L[4];
-        gather<BX, BY, BZ, CG>(a.tmp, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
-        if (!stored) continue;
+        ldr4(a.E + idx, E);
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -299,28 +278,29 @@ __device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView 
             acc += (double)(o[i].x * o[i].x + o[i].y * o[i].y);
         }
         st4(a.psi + idx, o);
-    }
+    });
 }
 
 template <typename R, int BX, int BY, int BZ>
 __global__ void GPE_BOUNDS(R) k_itp_a(const ItpArgs<R> a, const GridView G)
 {
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     const R sc = (R)a.scalars[0];
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
-        itp_brick_a<R, BX, BY, BZ, false>(a, G, b, s_rec[warp], sc);
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
+        itp_brick_a<R, BX, BY, BZ, false>(a, G, b, ws, sc);
 }
 
 template <typename R, int BX, int BY, int BZ>
-__global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, double *partials,
-                                               unsigned int *counter)
+__global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, double *partials, unsigned int *counter)
 {
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS)
-        itp_brick_b<R, BX, BY, BZ, false>(a, G, b, s_rec[warp], acc[0]);
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
+        itp_brick_b<R, BX, BY, BZ, false>(a, G, b, ws, acc[0]);
     double tot[1];
     if (reduce_finish<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         const double nrm = tot[0] * a.dV;
@@ -330,10 +310,10 @@ __global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, doub
 }
 
 template <typename R, int BX, int BY, int BZ>
-__global__ void GPE_BOUNDS(R) k_itp_wave(const ItpArgs<R> a, const GridView G, const Wave w,
-                                                  double *chunk_norm)
+__global__ void GPE_BOUNDS(R) k_itp_wave(const ItpArgs<R> a, const GridView G, const Wave w, double *chunk_norm)
 {
-    __shared__ BrickRec s_rec[WARPS][7];
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
     __shared__ bool s_last;
     const int warp = threadIdx.x >> 5;
     const R sc = (R)a.scalars[0];
@@ -345,12 +325,12 @@ __global__ void GPE_BOUNDS(R) k_itp_wave(const ItpArgs<R> a, const GridView G, c
         const int64_t b0 = (int64_t)c * w.cb;
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
         if (st == 0) {
-            for (int64_t b = b0 + warp; b < b1; b += WARPS) itp_brick_a<R, BX, BY, BZ, true>(a, G, b, s_rec[warp], sc);
+            for (int64_t b = b0 + warp; b < b1; b += NW) itp_brick_a<R, BX, BY, BZ, true>(a, G, b, ws, sc);
             publish(w, st, c);
             continue;
         }
         double acc = 0.0;
-        for (int64_t b = b0 + warp; b < b1; b += WARPS) itp_brick_b<R, BX, BY, BZ, true>(a, G, b, s_rec[warp], acc);
+        for (int64_t b = b0 + warp; b < b1; b += NW) itp_brick_b<R, BX, BY, BZ, true>(a, G, b, ws, acc);
         const double part = block_sum(acc);
         if (threadIdx.x == 0) chunk_norm[c] = part;
         publish(w, st, c);
@@ -405,27 +385,17 @@ struct ObsArgs {
 template <typename R, int BX, int BY, int BZ>
 __global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R> a, const GridView G)
 {
-    using S = Seg<BX, BY, BZ>;
     using CT = typename Cx<R>::T;
-    __shared__ BrickRec s_rec[WARPS][7];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
+    const int warp = threadIdx.x >> 5;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // norm, ekin, epot, eint, nonfinite
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < G.nb; b += (int64_t)gridDim.x * WARPS) {
-        BrickRec *Rr = s_rec[warp];
-        load_recs(Rr, G, b);
-#pragma unroll 1
-        for (int it = 0; it < S::NIT; ++it) {
-            const int q = it * 32 + lane;
-            uint32_t idx = 0;
-            const bool stored = seg_index(Rr[0], q, idx);
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
+        brick_apply<BX, BY, BZ, false>(ws, G, b, a.psi, Identity(), a.ihx2, a.ihy2, a.ihz2,
+                                       [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
             R V0[4], V1[4];
-            if (stored) {
-                ldr4(a.V0 + idx, V0);
-                if (a.V1) ldr4(a.V1 + idx, V1);
-            }
-            CT c[4], L[4];
-            gather<BX, BY, BZ, false>(a.psi, Rr, q, stored, idx, Identity(), a.ihx2, a.ihy2, a.ihz2, c, L);
-            if (!stored) continue;
+            ldr4(a.V0 + idx, V0);
+            if (a.V1) ldr4(a.V1 + idx, V1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!(V0[i] < (R)INFINITY)) continue;
@@ -437,7 +407,7 @@ __global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R> a, const GridView G)
                 acc[3] += (double)((R)0.5 * a.g * rho * rho);
                 acc[4] += (isfinite(c[i].x) && isfinite(c[i].y)) ? 0.0 : 1.0;
             }
-        }
+        });
     }
     double tot[5];
     if (reduce_finish<5>(acc, a.partials, a.counter, tot) && threadIdx.x == 0) {
@@ -734,27 +704,28 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
         GPE_LAUNCH_CHECK();
     }
     const GridView G = view(g);
-    const int th = brick_threads(g);
+    const int th = KernelCfg<R>::THREADS;
+    const size_t smem = smem_bytes<R, BX, BY, BZ>();
     if (g->sched == GPE_SCHED_WAVE) {
         GPE_TRY(ensure_wave(st));
         auto k = blend ? k_rk4_wave<R, BX, BY, BZ, true> : k_rk4_wave<R, BX, BY, BZ, false>;
-        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th), 4 * g->n_chunks);
+        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), 4 * g->n_chunks);
         for (int64_t n = 0; n < nsteps; ++n) {
             a.t_off = (double)n * p->dt;
-            k<<<nblk, th, 0, s>>>(a, G, make_wave(st, 4));
+            k<<<nblk, th, smem, s>>>(a, G, make_wave(st, 4));
             GPE_LAUNCH_CHECK();
             advance_wave(st, 4, nblk, false);
         }
         return GPE_OK;
     }
     auto k = blend ? k_rk4_staged<R, BX, BY, BZ, true> : k_rk4_staged<R, BX, BY, BZ, false>;
-    const int nblk = blocks_for(k, g, th);
+    const int nblk = blocks_for<R>(k, g, smem);
     // steps n0 .. n0+cnt-1 with stage times relative to the device clock
     auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
         for (int64_t n = 0; n < cnt; ++n) {
             a.t_off = (double)n * p->dt;
             for (int stg = 0; stg < 4; ++stg) {
-                k<<<nblk, th, 0, cs>>>(a, G, stg);
+                k<<<nblk, th, smem, cs>>>(a, G, stg);
                 GPE_LAUNCH_CHECK();
             }
         }
@@ -806,25 +777,26 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
     k_set_scalar<<<1, 1, 0, s>>>(st->red.scalars, 1.0);
     GPE_LAUNCH_CHECK();
     const GridView G = view(g);
-    const int th = brick_threads(g);
+    const int th = KernelCfg<R>::THREADS;
+    const size_t smem = smem_bytes<R, BX, BY, BZ>();
     if (g->sched == GPE_SCHED_WAVE) {
         GPE_TRY(ensure_wave(st));
         auto k = k_itp_wave<R, BX, BY, BZ>;
-        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th), 2 * g->n_chunks);
+        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), 2 * g->n_chunks);
         for (int64_t n = 0; n < nsteps; ++n) {
-            k<<<nblk, th, 0, s>>>(a, G, make_wave(st, 2), st->d_chunk_norm);
+            k<<<nblk, th, smem, s>>>(a, G, make_wave(st, 2), st->d_chunk_norm);
             GPE_LAUNCH_CHECK();
             advance_wave(st, 2, nblk, true);
         }
     } else {
         auto ka = k_itp_a<R, BX, BY, BZ>;
         auto kb = k_itp_b<R, BX, BY, BZ>;
-        const int nba = blocks_for(ka, g, th), nbb = blocks_for(kb, g, th);
+        const int nba = blocks_for<R>(ka, g, smem), nbb = blocks_for<R>(kb, g, smem);
         auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
             for (int64_t n = 0; n < cnt; ++n) {
-                ka<<<nba, th, 0, cs>>>(a, G);
+                ka<<<nba, th, smem, cs>>>(a, G);
                 GPE_LAUNCH_CHECK();
-                kb<<<nbb, th, 0, cs>>>(a, G, st->red.partials, st->red.counter);
+                kb<<<nbb, th, smem, cs>>>(a, G, st->red.partials, st->red.counter);
                 GPE_LAUNCH_CHECK();
             }
             return GPE_OK;
@@ -864,9 +836,9 @@ static int obs_run(const gpe_state *stc, double gg, double sb, cudaStream_t s)
     a.partials = st->red.partials;
     a.counter = st->red.counter;
     a.out = (gpe_obs *)(st->red.scalars + 2);
-    const int th = brick_threads(g);
+    const size_t smem = smem_bytes<R, BX, BY, BZ>();
     auto k = k_obs<R, BX, BY, BZ>;
-    k<<<blocks_for(k, g, th), th, 0, s>>>(a, view(g));
+    k<<<blocks_for<R>(k, g, smem), KernelCfg<R>::THREADS, smem, s>>>(a, view(g));
     GPE_LAUNCH_CHECK();
     return GPE_OK;
 }
