@@ -103,6 +103,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- workload
 WORKLOADS = {"shell1024": "SHELL_1024", "shell512": "SHELL_512"}
+EXTRA = ("ramp2048", "adjoint512", "batch")
 _workload_name = "shell1024"
 
 
@@ -390,14 +391,150 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- other workloads
+def _ramp_grid(gpe, rw):
+    b = rw.shell.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    p0 = gpe.make_potential(gpe.GPE_POT_HARMONIC, rw.W, rw.W, rw.W)
+    p1 = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, rw.shell.w, *rw.shell.axes)
+    return gpe.gpe_grid_create_blend(gb, p0, rw.cut0, p1, rw.cut1)
+
+
+def _core_state(gpe, inputs, rw, grid, dtype):
+    """Normalised parabolic core cloud sqrt(max(mu0 - V0, 0)) on the grid."""
+    idx, i, j, k = gpe.packed_coords(grid)
+    info = gpe.gpe_grid_get_info(grid)
+    b = rw.shell.box
+    out = np.zeros(info.n_packed, np.complex128)
+    x, y, z = b.x0 + i * b.hx, b.y0 + j * b.hy, b.z0 + k * b.hz
+    out[idx] = np.sqrt(np.maximum(rw.mu0_core - rw.v0(x, y, z), 0.0))
+    out *= math.sqrt(1.0 / (np.sum(np.abs(out) ** 2) * b.dV))
+    return np.ascontiguousarray(out.astype(np.complex64 if dtype == gpe.GPE_C64 else np.complex128))
+
+
+def run_extra(args):
+    """Ramp (2048^3, ~1e8 active), adjoint (512^3) and batch workloads: one
+    JSON line each, beside the headline line of the default run."""
+    import torch
+    from paper_2603_05447_gb300 import _build, gpe, inputs
+    from paper_2603_05447_gb300 import dist as gdist
+    rank, world, local = gdist.env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    gpe.load()
+    side = torch.cuda.Stream()
+    line = {"workload": args.workload, "n_gpus": world, "data": "synthetic"}
+    with torch.cuda.stream(side):
+        if args.workload in ("ramp2048", "adjoint512"):
+            rw = inputs.RAMP_2048 if args.workload == "ramp2048" else inputs.RAMP_512
+            grid = _ramp_grid(gpe, rw)
+            info = gpe.gpe_grid_get_info(grid)
+            st = gpe.gpe_state_create(grid, gpe.GPE_C64)
+            gpe.gpe_state_load(st, _core_state(gpe, inputs, rw, grid, gpe.GPE_C64), gpe.GPE_LAYOUT_COMPACT)
+            # the union region holds the shell potential at the trap centre and the trap
+            # potential on the shell: the explicit step must resolve the largest |V|
+            h = rw.shell.h
+            dt = 0.2 / (6.0 / h ** 2 + info.v_max)
+            nsteps = args.steps * STEPS_PER_BENCH
+            knots = inputs.monotone_knots(16, seed=3)
+            p = gpe.real_params(rw.shell.g, dt, gpe.GPE_V_BLEND, knots, nsteps * dt)
+            if args.workload == "ramp2048":
+                gpe.gpe_step_real(st, p, args.warmup * 10)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gpe.gpe_step_real(st, p, nsteps)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = gdist.max_over_ranks(e0.elapsed_time(e1))
+                o = gpe.gpe_observables(st, rw.shell.g, float(knots[-1]))
+                line.update(metric="ramp cell-steps/s (RK4, complex64, V(t) blend)", unit="cell-steps/s",
+                            value=info.n_active * nsteps * world / (ms / 1e3), n_active=info.n_active,
+                            n_packed=info.n_packed, steps=nsteps, ms_per_step=ms / nsteps, norm_after=o["norm"],
+                            dt=dt, v_max=info.v_max,
+                            config="2048^3 box, shell semi-axis 800 cells + harmonic core radius 0.24, g=5000, "
+                                   "16 seeded monotone knots over the run")
+            else:
+                tg = gpe.gpe_state_create(grid, gpe.GPE_C64)
+                gpe.gpe_state_copy(tg, st)
+                nsteps = 4000
+                K = 64
+                p = gpe.real_params(rw.shell.g, dt, gpe.GPE_V_BLEND, knots, nsteps * dt)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                tape = gpe.gpe_ramp_forward(st, p, nsteps, 0.0, K)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                loss, grad = gpe.gpe_ramp_backward(tape, tg, 16)
+                t2 = time.perf_counter()
+                gpe.gpe_tape_destroy(tape)
+                gpe.gpe_state_destroy(tg)
+                line.update(metric="adjoint ramp gradient (4000 RK4 steps, K=64, complex64 + FP64 gradient)",
+                            unit="s", value=t2 - t0, forward_s=t1 - t0, backward_s=t2 - t1,
+                            n_active=info.n_active, loss=loss, grad_norm=float(np.linalg.norm(grad)),
+                            forward_cell_steps_per_s=info.n_active * nsteps / (t1 - t0),
+                            config="512^3 box, shell semi-axis 200 cells + harmonic core, ~5e6 active, target = "
+                                   "initial state")
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(grid)
+        else:
+            shells = inputs.batch_shells(args.shells)
+            grids, states, cells = [], [], []
+            for wl in shells:
+                b = wl.box
+                gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+                pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+                g = gpe.gpe_grid_create_analytic(gb, pot, wl.V_cut)
+                grids.append(g)
+                cells.append(gpe.gpe_grid_get_info(g).n_active)
+            mine = gdist.shard(cells, world, rank)
+            for i in mine:
+                wl, g = shells[i], grids[i]
+                idx, ii, jj, kk = gpe.packed_coords(g)
+                b = wl.box
+                x, y, z = b.x0 + ii * b.hx, b.y0 + jj * b.hy, b.z0 + kk * b.hz
+                psi = np.zeros(gpe.gpe_grid_get_info(g).n_packed, np.complex64)
+                psi[idx] = np.sqrt(np.maximum(wl.mu0 - wl.potential(x, y, z), 0.0) / wl.g)
+                st = gpe.gpe_state_create(g, gpe.GPE_C64)
+                gpe.gpe_state_load(st, psi, gpe.GPE_LAYOUT_COMPACT)
+                states.append(st)
+            batch = gpe.gpe_batch_create(states)
+            params = [gpe.gpe_imag_params(shells[i].g, shells[i].stable_dt() * 20, 1.0) for i in mine]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, conv, steps, obs = gpe.gpe_batch_ground_state(batch, params, args.tol, 100,
+                                                              args.steps * STEPS_PER_BENCH, check=False)
+            el = gdist.max_over_ranks(time.perf_counter() - t0)
+            done = gdist.sum_over_ranks(sum(cells[i] * s for i, s in zip(mine, steps)))
+            line.update(metric="batched ground states: active-cell ITP steps/s (complex64, FP64 norms)",
+                        unit="cell-steps/s", value=done / el, shells=len(shells), n_active_total=int(sum(cells)),
+                        converged=int(gdist.sum_over_ranks(sum(conv))), tol_dmu=args.tol,
+                        max_steps=args.steps * STEPS_PER_BENCH, seconds=el, scaling="strong",
+                        config="seeded uneven ellipsoidal shells (radius U[0.5,1] x 360 cells, aspects U[0.7,1], "
+                               "thickness U[4,10] cells, g U[100,3000]), one persistent launch, graph-replayed")
+            gpe.gpe_batch_destroy(batch)
+            for st in states:
+                gpe.gpe_state_destroy(st)
+            for g in grids:
+                gpe.gpe_grid_destroy(g)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="shell1024",
-                    help="shell512 is the smaller case used for ncu captures")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(EXTRA), default="shell1024",
+                    help="shell512 is the smaller case used for ncu captures; ramp2048, adjoint512 and batch "
+                         "time the other workloads (one JSON line each)")
+    ap.add_argument("--shells", type=int, default=64, help="batch workload: number of shells")
+    ap.add_argument("--tol", type=float, default=1e-8, help="batch workload: |dmu| tolerance")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident complex64 timing only (for profiling runs)")
     ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront")
@@ -411,6 +548,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in EXTRA:
+        run_extra(args)
     else:
         run_ours(args)
 

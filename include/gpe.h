@@ -220,6 +220,13 @@ int gpe_state_store(const gpe_state *st, void *psi, int layout, int on_device,
 /* dst <- src (same grid and dtype).  Asynchronous. */
 int gpe_state_copy(gpe_state *dst, const gpe_state *src, gpe_stream stream);
 
+/* Failure detection self-test: one warp waits (with the same bounded wait the
+ * wavefront schedule uses) for a completion stamp that nothing sets; the wait
+ * gives up after limit_s seconds (0 < limit_s <= 10) and reports it.  Sets
+ * *timed_out (1 expected) and *waited_s (may be NULL).  No GPU fault or hang
+ * is involved: the kernel returns and the context stays usable.  Synchronous. */
+int gpe_wait_selftest(double limit_s, int *timed_out, double *waited_s);
+
 /* Step loops on the staged schedule are captured in CUDA graphs of
  * steps_per_graph steps (default 32; 0 disables) and replayed, when the
  * stream is not the legacy default stream and a call asks for at least that

@@ -116,8 +116,10 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 constexpr long long WAIT_ITERS = 40000000LL;           // backstop if the timer stalls
 
 // Called by all 32 lanes of one warp: wait until done[c] >= target for every
-// chunk c in [lo, hi].  Returns false (and sets *err) if the wait runs out.
-__device__ bool wait_chunks(const uint32_t *done, int lo, int hi, uint32_t target, unsigned long long *err)
+// chunk c in [lo, hi].  Returns false (and sets *err) if the wait runs out
+// after limit_ns.
+__device__ bool wait_chunks(const uint32_t *done, int lo, int hi, uint32_t target, unsigned long long *err,
+                            unsigned long long limit_ns = WAIT_NS)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long t0 = global_ns();
@@ -125,11 +127,21 @@ __device__ bool wait_chunks(const uint32_t *done, int lo, int hi, uint32_t targe
         bool ok = true;
         for (int i = lo + lane; i <= hi; i += 32) ok = ok && (ld_acquire(done + i) >= target);
         if (__all_sync(0xffffffffu, ok)) return true;
-        if (global_ns() - t0 > WAIT_NS) break;
+        if (global_ns() - t0 > limit_ns) break;
         __nanosleep(200);
     }
     if (lane == 0) atomicOr(err, 1ull);
     return false;
+}
+
+// Self-test of the bounded wait: one warp waits for a completion stamp that
+// nothing sets; the wait must give up after limit_ns and report it.
+__global__ void k_wait_selftest(const uint32_t *flags, unsigned long long *err, unsigned long long limit_ns,
+                                unsigned long long *elapsed)
+{
+    const unsigned long long t0 = global_ns();
+    wait_chunks(flags, 0, 0, 1u, err, limit_ns);
+    if (threadIdx.x == 0) *elapsed = global_ns() - t0;
 }
 
 // Invalidate, without write-back, the L2 lines lying wholly inside
@@ -907,6 +919,31 @@ extern "C" int gpe_state_destroy(gpe_state *st)
     if (st->h_obs) cudaFreeHost(st->h_obs);
     st->grid->n_states--;
     delete st;
+    return GPE_OK;
+}
+
+extern "C" int gpe_wait_selftest(double limit_s, int *timed_out, double *waited_s)
+{
+    if (!timed_out || !(limit_s > 0) || limit_s > 10.0) return fail(GPE_ERR_ARG, "need 0 < limit_s <= 10 and timed_out");
+    uint32_t *flags = nullptr;
+    unsigned long long *w = nullptr;
+    GPE_TRY(dev_alloc_t(&flags, 1));
+    int rc = dev_alloc_t(&w, 2);
+    if (rc == GPE_OK) rc = dev_zero(flags, sizeof(uint32_t));
+    if (rc == GPE_OK) rc = dev_zero(w, 2 * sizeof(unsigned long long));
+    unsigned long long h[2] = {0, 0};
+    if (rc == GPE_OK) {
+        k_wait_selftest<<<1, 32>>>(flags, w, (unsigned long long)(limit_s * 1e9), w + 1);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof h, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "wait self-test", __FILE__, __LINE__);
+    }
+    dev_free(flags);
+    dev_free(w);
+    if (rc != GPE_OK) return rc;
+    *timed_out = h[0] != 0;
+    if (waited_s) *waited_s = (double)h[1] * 1e-9;
     return GPE_OK;
 }
 

@@ -139,6 +139,7 @@ _SIGS = {
     "gpe_observables": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(gpe_obs), _P]),
     "gpe_overlap": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P]),
     "gpe_state_set_graph": (C.c_int, [_P, C.c_int]),
+    "gpe_wait_selftest": (C.c_int, [C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "gpe_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P)]),
     "gpe_batch_ground_state": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_double, C.c_int64, C.c_int64,
                                          C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(gpe_obs), _P]),
@@ -439,6 +440,14 @@ def gpe_overlap(a, b, stream=None) -> complex:
     out = (C.c_double * 2)()
     _check(load().gpe_overlap(a, b, out, stream_handle(stream)))
     return complex(out[0], out[1])
+
+
+def gpe_wait_selftest(limit_s):
+    """Returns (timed_out, waited seconds)."""
+    t = C.c_int()
+    w = C.c_double()
+    _check(load().gpe_wait_selftest(float(limit_s), C.byref(t), C.byref(w)))
+    return bool(t.value), w.value
 
 
 def gpe_state_set_graph(state, steps_per_graph):

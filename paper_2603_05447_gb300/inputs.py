@@ -217,3 +217,77 @@ def monotone_knots(n: int = 16, seed: int = 3) -> np.ndarray:
     rng = np.random.default_rng(seed)
     inner = np.sort(rng.uniform(0.0, 1.0, n - 2))
     return np.concatenate([[0.0], inner, [1.0]])
+
+
+# ---------------------------------------------------------------- ramps
+@dataclass(frozen=True)
+class RampWorkload:
+    """Hollowing-out ramp: V(t) = (1 - s(t)) V0 + s(t) V1 from a compact
+    harmonic trap V0 = 1/2 W^2 r^2 to the thin shell V1 of ``shell``, on a
+    cubic box; the region of interest is the union {V0 < cut0} U {V1 < cut1}.
+    W is fixed by the Thomas-Fermi radius of N atoms at coupling g being
+    ``core_radius`` / sqrt(cut_factor) (so the harmonic region has radius
+    ``core_radius``); both cutoffs are cut_factor times the reference chemical
+    potentials.  Workload constants, not computed results."""
+    shell: ShellWorkload
+    core_radius: float
+
+    @property
+    def mu0_core(self):
+        # Closed-form workload constant: a parabolic (Thomas-Fermi-like) cloud
+        # of N atoms in W^2 r^2 / 2 has mu = (15 g N W^3 / (4 pi))^(2/5) / 2
+        # and radius R = sqrt(2 mu) / W; W is picked so that R is the target.
+        R = self.core_radius / math.sqrt(self.shell.cut_factor)
+        c = (15.0 * self.shell.g * self.shell.N / (4.0 * math.pi)) ** 0.4
+        W = (c / R ** 2) ** (1.0 / 0.8)
+        return 0.5 * W * W * R * R
+
+    @property
+    def W(self):
+        R = self.core_radius / math.sqrt(self.shell.cut_factor)
+        return math.sqrt(2.0 * self.mu0_core) / R
+
+    @property
+    def cut0(self):
+        return self.shell.cut_factor * self.mu0_core
+
+    @property
+    def cut1(self):
+        return self.shell.V_cut
+
+    @property
+    def v0(self):
+        return Harmonic(self.W, self.W, self.W)
+
+    def stable_dt(self, courant: float = 0.2):
+        h = self.shell.h
+        lam = 6.0 / h ** 2 + max(self.cut0, self.cut1) + 2.0 * max(self.mu0_core, self.shell.mu0)
+        return courant / lam
+
+
+# 2048^3 box, shell semi-axis 800 cells (~7.7e7 active) plus a harmonic core of
+# radius 0.24 (~3e7 active): about 1e8 active cells, g = 5000
+RAMP_2048 = RampWorkload(ShellWorkload(n=2048, a_cells=800.0, g=5000.0), core_radius=0.24)
+# 512^3 box, ~5e6 active: the adjoint workload
+RAMP_512 = RampWorkload(ShellWorkload(n=512, a_cells=200.0, g=5000.0), core_radius=0.24)
+# 48^3 version for parity tests
+RAMP_48 = RampWorkload(ShellWorkload(n=48, a_cells=19.0, g=5000.0), core_radius=0.24)
+
+
+def batch_shells(n: int = 64, seed: int = 4, scale_cells: float = 360.0):
+    """Seeded batch of uneven ellipsoidal shells: radius r ~ U[0.5, 1] (semi-axis
+    r * scale_cells cells), aspect ratios b/a, c/a ~ U[0.7, 1], thickness
+    ~ U[4, 10] cells, g ~ U[100, 3000]; the box is the smallest cube holding
+    the active band with a 4-cell margin."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        r = rng.uniform(0.5, 1.0)
+        ar = (1.0, rng.uniform(0.7, 1.0), rng.uniform(0.7, 1.0))
+        width = rng.uniform(4.0, 10.0)
+        g = rng.uniform(100.0, 3000.0)
+        a_cells = r * scale_cells
+        band = math.sqrt(5.0) * width / 2.0
+        nbox = int(2 * math.ceil(a_cells + band + 4))
+        out.append(ShellWorkload(n=nbox, a_cells=a_cells, g=g, width_cells=width, axes=ar))
+    return out
