@@ -167,50 +167,60 @@ __device__ __forceinline__ CT ld1(const CT *p)
     return CG ? __ldcg(p) : *p;
 }
 
-// Per-warp workspace: the brick's cells with the y and z face halos as whole
-// rows (BX cells per row, rows y = -1..BY, planes z = -1..BZ), the x face
-// halos as separate columns (so every row, and every segment, starts on a
-// 16-byte boundary for vector shared-memory access), the records of the brick
-// and its six face neighbours, and the brick's stored segments in order.
+// Per-warp workspace.  The brick's segments, with the y and z face halos as
+// whole rows (rows y = -1..BY, planes z = -1..BZ), are stored as UPS planes of
+// 16-byte units: unit u of every segment slot is contiguous, so lanes that
+// take consecutive segments touch consecutive 16-byte units (no shared-memory
+// bank conflicts).  The x face halos are separate columns.  Then the records
+// of the brick and its six face neighbours and the brick's stored segments in
+// order.
 template <typename CT, int BX, int BY, int BZ>
 struct WarpSpace {
-    static constexpr int TY = BY + 2, TZ = BZ + 2;
+    static constexpr int SX = BX / 4, TY = BY + 2, TZ = BZ + 2;
+    static constexpr int NSLOT = SX * TY * TZ;                   // segment slots incl. y/z halos
+    static constexpr int UPS = (int)(4 * sizeof(CT) / 16);       // 16-byte units per segment
+    static constexpr int CPU_ = 4 / UPS;                         // cells per unit
     static constexpr int NSEG = Seg<BX, BY, BZ>::NSEG;
-    static constexpr int ROW = BX, PLANE = BX * TY;
-    __device__ __forceinline__ static int m(int x, int y, int z) { return x + BX * ((y + 1) + TY * (z + 1)); }
+    static constexpr int ROW = SX, PLANE = SX * TY;              // slot strides in y and z
+    __device__ __forceinline__ static int slot(int hx, int y, int z) { return hx + SX * ((y + 1) + TY * (z + 1)); }
     __device__ __forceinline__ static int h(int y, int z) { return y + BY * z; }
-    CT main[BX * TY * TZ];
+    uint4 units[UPS][NSLOT];
     CT xlo[BY * BZ];  // x = -1
     CT xhi[BY * BZ];  // x = BX
     BrickRec rec[7];
     uint8_t list[NSEG];
     uint8_t pad[(16 - (NSEG % 16)) % 16];
-};
 
-// 4 complex values to / from shared memory at a 16-byte aligned address
-__device__ __forceinline__ void sget4(const float2 *p, float2 (&v)[4])
-{
-    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
-    v[0] = make_float2(a.x, a.y);
-    v[1] = make_float2(a.z, a.w);
-    v[2] = make_float2(b.x, b.y);
-    v[3] = make_float2(b.z, b.w);
-}
-__device__ __forceinline__ void sget4(const double2 *p, double2 (&v)[4])
-{
+    __device__ __forceinline__ void get(int s, CT (&v)[4]) const
+    {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = p[i];
-}
-__device__ __forceinline__ void sput4(float2 *p, const float2 (&v)[4])
-{
-    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    reinterpret_cast<float4 *>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-}
-__device__ __forceinline__ void sput4(double2 *p, const double2 (&v)[4])
-{
+        for (int u = 0; u < UPS; ++u) {
+            const uint4 w = units[u][s];
+            const CT *c = reinterpret_cast<const CT *>(&w);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) p[i] = v[i];
-}
+            for (int i = 0; i < CPU_; ++i) v[u * CPU_ + i] = c[i];
+        }
+    }
+    __device__ __forceinline__ void put(int s, const CT (&v)[4])
+    {
+#pragma unroll
+        for (int u = 0; u < UPS; ++u) {
+            uint4 w;
+            CT *c = reinterpret_cast<CT *>(&w);
+#pragma unroll
+            for (int i = 0; i < CPU_; ++i) c[i] = v[u * CPU_ + i];
+            units[u][s] = w;
+        }
+    }
+    __device__ __forceinline__ CT first(int s) const  // cell 0 of slot s
+    {
+        return reinterpret_cast<const CT *>(&units[0][s])[0];
+    }
+    __device__ __forceinline__ CT last(int s) const  // cell 3 of slot s
+    {
+        return reinterpret_cast<const CT *>(&units[UPS - 1][s])[CPU_ - 1];
+    }
+};
 
 template <typename R, int BX, int BY, int BZ>
 constexpr size_t smem_bytes()
@@ -270,7 +280,7 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         CT v[4];
         seg4(R0, q, v);
         const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-        sput4(ws.main + W::m(4 * hx, y, z), v);
+        ws.put(W::slot(hx, y, z), v);
         const bool stored = (R0.m[q >> 5] >> (q & 31)) & 1u;
         const unsigned bal = __ballot_sync(0xffffffffu, stored);
         if (stored) ws.list[nst + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
@@ -281,7 +291,7 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         const int face = u / S::PLANE, qc = u % S::PLANE;
         CT v[4];
         seg4(ws.rec[5 + face], face == 0 ? qc + S::PLANE * (BZ - 1) : qc, v);
-        sput4(ws.main + W::m(4 * (qc % S::SX), qc / S::SX, face == 0 ? -1 : BZ), v);
+        ws.put(W::slot(qc % S::SX, qc / S::SX, face == 0 ? -1 : BZ), v);
     }
     // -y / +y faces: segments of the neighbours' boundary rows
     for (int u = lane; u < 2 * S::SX * BZ; u += 32) {
@@ -289,7 +299,7 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         const int hx = v_ % S::SX, z = v_ / S::SX;
         CT v[4];
         seg4(ws.rec[3 + face], hx + S::SX * (face == 0 ? BY - 1 : 0) + S::PLANE * z, v);
-        sput4(ws.main + W::m(4 * hx, face == 0 ? -1 : BY, z), v);
+        ws.put(W::slot(hx, face == 0 ? -1 : BY, z), v);
     }
     // -x / +x faces: single cells (x = BX-1 of the -x brick, x = 0 of the +x brick)
     for (int u = lane; u < 2 * BY * BZ; u += 32) {
@@ -309,15 +319,15 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
     for (int r = lane; r < nst; r += 32) {
         const int q = ws.list[r];
         const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-        const int base = W::m(4 * hx, y, z);
+        const int sl = W::slot(hx, y, z);
         CT c[4], ym[4], yp[4], zm[4], zp[4], L[4];
-        sget4(ws.main + base, c);
-        sget4(ws.main + base - W::ROW, ym);
-        sget4(ws.main + base + W::ROW, yp);
-        sget4(ws.main + base - W::PLANE, zm);
-        sget4(ws.main + base + W::PLANE, zp);
-        const CT xm = hx == 0 ? ws.xlo[W::h(y, z)] : ws.main[base - 1];
-        const CT xp = hx == S::SX - 1 ? ws.xhi[W::h(y, z)] : ws.main[base + 4];
+        ws.get(sl, c);
+        ws.get(sl - W::ROW, ym);
+        ws.get(sl + W::ROW, yp);
+        ws.get(sl - W::PLANE, zm);
+        ws.get(sl + W::PLANE, zp);
+        const CT xm = hx == 0 ? ws.xlo[W::h(y, z)] : ws.last(sl - 1);
+        const CT xp = hx == S::SX - 1 ? ws.xhi[W::h(y, z)] : ws.first(sl + 1);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const CT l = i == 0 ? xm : c[i - 1];
