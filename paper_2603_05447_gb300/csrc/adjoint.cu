@@ -315,11 +315,16 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
     f.ramp.T = p.T_ramp;
     f.ramp.n_knots = p.n_knots;
     for (int k = 0; k < GPE_MAX_KNOTS; ++k) f.ramp.knots[k] = p.knots[k];
-    auto kf = k_rk4_staged<R, BX, BY, BZ, true>;
+    typename Rk4Stages<R, BX, BY, BZ>::K kf[4];
     auto ka = k_adj_stage<R, BX, BY, BZ, true>;
     const size_t smem = smem_bytes<R, BX, BY, BZ>();
     const int th = KernelCfg<R>::THREADS;
-    const int nbf = adj_blocks<R>(kf, g, smem), nba = adj_blocks<R>(ka, g, smem);
+    int nbf[4];
+    for (int stg = 0; stg < 4; ++stg) {
+        kf[stg] = Rk4Stages<R, BX, BY, BZ>::get(true, stg);
+        nbf[stg] = adj_blocks<R>(kf[stg], g, smem);
+    }
+    const int nba = adj_blocks<R>(ka, g, smem);
     AdjArgs<R> a{};
     a.lam = lam;
     a.lam_out = lam;
@@ -344,7 +349,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
             f.y0 = seg + (m + 1) * np;
             f.t_off = t->t0 + (double)(j * t->K + m) * p.dt;
             for (int stg = 0; stg < 4; ++stg) {
-                kf<<<nbf, th, smem, s>>>(f, G, stg);
+                kf[stg]<<<nbf[stg], th, smem, s>>>(f, G);
                 GPE_LAUNCH_CHECK();
             }
         }
@@ -353,7 +358,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
             f.y0 = seg + m * np;
             f.t_off = tm;
             for (int stg = 0; stg < 3; ++stg) {  // Y2, Y3, Y4
-                kf<<<nbf, th, smem, s>>>(f, G, stg);
+                kf[stg]<<<nbf[stg], th, smem, s>>>(f, G);
                 GPE_LAUNCH_CHECK();
             }
             // stages 4, 3, 2, 1 of the reverse sweep

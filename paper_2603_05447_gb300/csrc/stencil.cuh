@@ -6,6 +6,8 @@
 
 #include "gpe_internal.cuh"
 
+#include <type_traits>
+
 namespace gpe {
 
 // Stencil kernels run one brick per warp; a block holds NW warps, each with
@@ -244,63 +246,95 @@ __device__ __forceinline__ void put4(CT *t, const CT (&v)[4])
     t[3] = v[3];
 }
 
-// Apply body(idx, c, L) to every stored segment of brick b, one warp: idx is
-// the packed index of the segment's first cell, c[4] its values and L[4]
-// their 7-point Laplacians (Eq. (B1)), all taken from src after xf(value,
-// packed index).  The warp first stages the brick's stored segments (32-byte
-// vector loads, coalesced along the packed run) and the face halos from the
-// neighbour bricks into its tile; absent cells read as zero.  Lanes then take
-// the stored segments in order, so the packed indices of a warp's segments
-// are consecutive and the bodies' own-cell loads and stores coalesce.
-template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename BODY>
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only): the tile
+// fill issues every copy of a brick before waiting on any of them, so a warp
+// keeps its whole tile (and its body's prefetched operands) in flight without
+// staging them in registers.  valid == false writes 16 zero bytes.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// no operands to prefetch
+struct NoPre {
+    struct P {};
+    __device__ __forceinline__ P operator()(uint32_t) const { return P{}; }
+};
+
+// Apply body(idx, pre, c, L) to every stored segment of brick b, one warp:
+// idx is the packed index of the segment's first cell, pre what load(idx)
+// returned for it, c[4] its values and L[4] their 7-point Laplacians
+// (Eq. (B1)), all taken from src after xf(value, packed index).  The warp
+// stages the brick's stored segments (contiguous along the packed run) and
+// the face halos from the neighbour bricks in its tile; absent cells read as
+// zero.  Lanes then take the stored segments in order, so the packed indices
+// of a warp's segments are consecutive and the bodies' own-cell loads and
+// stores coalesce.  The first 32 segments' operands are loaded while the tile
+// is in flight.  With xf the identity the tile is filled by cp.async;
+// otherwise through registers, where xf is applied.
+template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename LOAD, typename BODY>
 __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b,
-                                            const CT *src, XF xf, R ihx2, R ihy2, R ihz2, BODY body)
+                                            const CT *src, XF xf, R ihx2, R ihy2, R ihz2, LOAD load, BODY body)
 {
     using S = Seg<BX, BY, BZ>;
     using W = WarpSpace<CT, BX, BY, BZ>;
+    constexpr bool ASYNC = std::is_same<XF, Identity>::value;
     const int lane = threadIdx.x & 31;
     load_recs(ws.rec, G, b);
     const BrickRec &R0 = ws.rec[0];
-    auto seg4 = [&](const BrickRec &r, int q, CT(&v)[4]) {
-        uint32_t j;
-        if (seg_index(r, q, j)) {
-            ld4<CG>(src + j, v);
+    const int nst = __popc(R0.m[0]) + __popc(R0.m[1]) + __popc(R0.m[2]) + __popc(R0.m[3]);
+    // one segment (4 cells) into tile slot sl
+    auto seg_to = [&](const BrickRec &r, int q, int sl) {
+        uint32_t j = 0;
+        const bool ok = seg_index(r, q, j);
+        if constexpr (ASYNC) {
+            const char *g = reinterpret_cast<const char *>(src + (ok ? j : 0u));
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = xf(v[i], j + i);
+            for (int u = 0; u < W::UPS; ++u) cp_async16(&ws.units[u][sl], g + 16 * u, ok);
         } else {
+            CT v[4];
+            if (ok) {
+                ld4<CG>(src + j, v);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = czero<CT>();
+                for (int i = 0; i < 4; ++i) v[i] = xf(v[i], j + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = czero<CT>();
+            }
+            ws.put(sl, v);
         }
     };
     // interior: stored segments from the packed run, zeros elsewhere
-    int nst = 0;
+    int nl = 0;
 #pragma unroll
     for (int it = 0; it < S::NIT; ++it) {
         const int q = it * 32 + lane;
-        CT v[4];
-        seg4(R0, q, v);
         const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-        ws.put(W::slot(hx, y, z), v);
+        seg_to(R0, q, W::slot(hx, y, z));
         const bool stored = (R0.m[q >> 5] >> (q & 31)) & 1u;
         const unsigned bal = __ballot_sync(0xffffffffu, stored);
-        if (stored) ws.list[nst + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
-        nst += __popc(bal);
+        if (stored) ws.list[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
+        nl += __popc(bal);
     }
     // -z / +z faces: whole segments of the neighbours' boundary planes
     for (int u = lane; u < 2 * S::PLANE; u += 32) {
         const int face = u / S::PLANE, qc = u % S::PLANE;
-        CT v[4];
-        seg4(ws.rec[5 + face], face == 0 ? qc + S::PLANE * (BZ - 1) : qc, v);
-        ws.put(W::slot(qc % S::SX, qc / S::SX, face == 0 ? -1 : BZ), v);
+        seg_to(ws.rec[5 + face], face == 0 ? qc + S::PLANE * (BZ - 1) : qc,
+               W::slot(qc % S::SX, qc / S::SX, face == 0 ? -1 : BZ));
     }
     // -y / +y faces: segments of the neighbours' boundary rows
     for (int u = lane; u < 2 * S::SX * BZ; u += 32) {
         const int face = u / (S::SX * BZ), v_ = u % (S::SX * BZ);
         const int hx = v_ % S::SX, z = v_ / S::SX;
-        CT v[4];
-        seg4(ws.rec[3 + face], hx + S::SX * (face == 0 ? BY - 1 : 0) + S::PLANE * z, v);
-        ws.put(W::slot(hx, face == 0 ? -1 : BY, z), v);
+        seg_to(ws.rec[3 + face], hx + S::SX * (face == 0 ? BY - 1 : 0) + S::PLANE * z,
+               W::slot(hx, face == 0 ? -1 : BY, z));
     }
+    // operands of the first 32 stored segments, while the tile is in flight
+    typename std::decay<decltype(load(0u))>::type p0{};
+    if (lane < nst) p0 = load(R0.off + 4u * (uint32_t)lane);
     // -x / +x faces: single cells (x = BX-1 of the -x brick, x = 0 of the +x brick)
     for (int u = lane; u < 2 * BY * BZ; u += 32) {
         const int face = u / (BY * BZ), v_ = u % (BY * BZ);
@@ -314,9 +348,10 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         }
         (face == 0 ? ws.xlo : ws.xhi)[W::h(y, z)] = v;
     }
+    if constexpr (ASYNC) cp_async_wait_all();
     __syncwarp();
     // stored segments: Laplacian from the tile, then the body
-    for (int r = lane; r < nst; r += 32) {
+    auto segment = [&](int r, const auto &pre) {
         const int q = ws.list[r];
         const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
         const int sl = W::slot(hx, y, z);
@@ -337,8 +372,21 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
             L[i].y = (rr.y - 2 * c[i].y + l.y) * ihx2 + (yp[i].y - 2 * c[i].y + ym[i].y) * ihy2 +
                      (zp[i].y - 2 * c[i].y + zm[i].y) * ihz2;
         }
-        body(R0.off + 4u * (uint32_t)r, c, L);
-    }
+        body(R0.off + 4u * (uint32_t)r, pre, c, L);
+    };
+    if (lane < nst) segment(lane, p0);
+    for (int r = lane + 32; r < nst; r += 32) segment(r, load(R0.off + 4u * (uint32_t)r));
+}
+
+// the same without prefetched operands: body(idx, c, L)
+template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename BODY>
+__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b,
+                                            const CT *src, XF xf, R ihx2, R ihy2, R ihz2, BODY body)
+{
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, src, xf, ihx2, ihy2, ihz2, NoPre(),
+                                [&](uint32_t idx, const NoPre::P &, const CT(&c)[4], const CT(&L)[4]) {
+                                    body(idx, c, L);
+                                });
 }
 
 // one-time launch preparation of a stencil kernel: dynamic shared memory
@@ -443,26 +491,36 @@ __device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
     return (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + c * a.dtd);
 }
 
-// One RK4 stage on brick b, one warp, lane = segment within each group of 32.
-template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG>
-__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int st, int64_t b,
+// One RK4 stage (st = 0..3) on brick b, one warp, lane = segment within each
+// group of 32.  The stage is a template argument so that each stage keeps
+// only its own prefetched operands in registers.
+template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG, int st>
+__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int64_t b,
                                           WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R s)
 {
     using CT = typename Cx<R>::T;
     const CT *yin = st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4;
     CT *yout = st == 0 ? a.y2 : st == 1 ? a.y3 : st == 2 ? a.y4 : a.y0;
     const R k = (st == 2) ? a.dt : (st == 3 ? a.dt / (R)6 : a.dt / (R)2);
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, yin, Identity(), a.ihx2, a.ihy2, a.ihz2,
-                                [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
-        R V0[4], V1[4];
-        CT y0[4], y2[4], y3[4];
-        ldr4(a.V0 + idx, V0);
-        if (BLEND) ldr4(a.V1 + idx, V1);
-        if (st > 0) ld4<CG>(a.y0 + idx, y0);
-        if (st == 3) {
-            ld4<CG>(a.y2 + idx, y2);
-            ld4<CG>(a.y3 + idx, y3);
+    constexpr int NV = BLEND ? 4 : 1, NY0 = st > 0 ? 4 : 1, NY23 = st == 3 ? 4 : 1;
+    struct P {
+        R V0[4], V1[NV];
+        CT y0[NY0], y2[NY23], y3[NY23];
+    };
+    auto load = [&](uint32_t idx) {
+        P p;
+        ldr4(a.V0 + idx, p.V0);
+        if constexpr (BLEND) ldr4(a.V1 + idx, p.V1);
+        if constexpr (st > 0) ld4<CG>(a.y0 + idx, p.y0);
+        if constexpr (st == 3) {
+            ld4<CG>(a.y2 + idx, p.y2);
+            ld4<CG>(a.y3 + idx, p.y3);
         }
+        return p;
+    };
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, yin, Identity(), a.ihx2, a.ihy2, a.ihz2, load,
+                                [&](uint32_t idx, const P &p, const CT(&c)[4], const CT(&L)[4]) {
+        const R(&V0)[4] = p.V0;
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -470,35 +528,51 @@ __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G,
                 o[i] = czero<CT>();
                 continue;
             }
-            const R V = BLEND ? ((R)1 - s) * V0[i] + s * V1[i] : V0[i];
+            R V = V0[i];
+            if constexpr (BLEND) V = ((R)1 - s) * V0[i] + s * p.V1[i];
             const R w = V + a.g * (c[i].x * c[i].x + c[i].y * c[i].y);
             const R hr = (R)(-0.5) * L[i].x + w * c[i].x;
             const R hi = (R)(-0.5) * L[i].y + w * c[i].y;
             // f = -i (hr + i hi) = hi - i hr
-            if (st == 0) {
+            if constexpr (st == 0) {
                 o[i].x = c[i].x + k * hi;
                 o[i].y = c[i].y - k * hr;
-            } else if (st < 3) {
-                o[i].x = y0[i].x + k * hi;
-                o[i].y = y0[i].y - k * hr;
+            } else if constexpr (st < 3) {
+                o[i].x = p.y0[i].x + k * hi;
+                o[i].y = p.y0[i].y - k * hr;
             } else {
-                o[i].x = (-y0[i].x + y2[i].x + (R)2 * y3[i].x + c[i].x) / (R)3 + k * hi;
-                o[i].y = (-y0[i].y + y2[i].y + (R)2 * y3[i].y + c[i].y) / (R)3 - k * hr;
+                o[i].x = (-p.y0[i].x + p.y2[i].x + (R)2 * p.y3[i].x + c[i].x) / (R)3 + k * hi;
+                o[i].y = (-p.y0[i].y + p.y2[i].y + (R)2 * p.y3[i].y + c[i].y) / (R)3 - k * hr;
             }
         }
         st4(yout + idx, o);
     });
 }
 
-template <typename R, int BX, int BY, int BZ, bool BLEND>
-__global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G, int st)
+template <typename R, int BX, int BY, int BZ, bool BLEND, int ST>
+__global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G)
 {
     constexpr int NW = KernelCfg<R>::NW;
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
-    const R s = stage_s<R, BLEND>(a, st);
+    const R s = stage_s<R, BLEND>(a, ST);
     for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
-        rk4_brick<R, BX, BY, BZ, BLEND, false>(a, G, st, b, ws, s);
+        rk4_brick<R, BX, BY, BZ, BLEND, false, ST>(a, G, b, ws, s);
 }
+
+// the four stage kernels of one shape, static (BLEND false) or blended
+template <typename R, int BX, int BY, int BZ>
+struct Rk4Stages {
+    using K = void (*)(RkArgs<R>, GridView);
+    static K get(bool blend, int st)
+    {
+        static const K t[2][4] = {
+            {k_rk4_staged<R, BX, BY, BZ, false, 0>, k_rk4_staged<R, BX, BY, BZ, false, 1>,
+             k_rk4_staged<R, BX, BY, BZ, false, 2>, k_rk4_staged<R, BX, BY, BZ, false, 3>},
+            {k_rk4_staged<R, BX, BY, BZ, true, 0>, k_rk4_staged<R, BX, BY, BZ, true, 1>,
+             k_rk4_staged<R, BX, BY, BZ, true, 2>, k_rk4_staged<R, BX, BY, BZ, true, 3>}};
+        return t[blend ? 1 : 0][st];
+    }
+};
 
 }  // namespace gpe

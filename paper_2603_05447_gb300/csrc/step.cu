@@ -213,7 +213,14 @@ __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, co
         wait_for(w, st, c);
         const int64_t b0 = (int64_t)c * w.cb;
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
-        for (int64_t b = b0 + warp; b < b1; b += NW) rk4_brick<R, BX, BY, BZ, BLEND, true>(a, G, st, b, ws, s[st]);
+        for (int64_t b = b0 + warp; b < b1; b += NW) {
+            switch (st) {
+            case 0: rk4_brick<R, BX, BY, BZ, BLEND, true, 0>(a, G, b, ws, s[0]); break;
+            case 1: rk4_brick<R, BX, BY, BZ, BLEND, true, 1>(a, G, b, ws, s[1]); break;
+            case 2: rk4_brick<R, BX, BY, BZ, BLEND, true, 2>(a, G, b, ws, s[2]); break;
+            default: rk4_brick<R, BX, BY, BZ, BLEND, true, 3>(a, G, b, ws, s[3]); break;
+            }
+        }
         publish(w, st, c);
         if (st == 3) {
             // y2 and y3 of this chunk have no reader left in this step
@@ -730,14 +737,18 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
         }
         return GPE_OK;
     }
-    auto k = blend ? k_rk4_staged<R, BX, BY, BZ, true> : k_rk4_staged<R, BX, BY, BZ, false>;
-    const int nblk = blocks_for<R>(k, g, smem);
+    typename Rk4Stages<R, BX, BY, BZ>::K k[4];
+    int nblk[4];
+    for (int stg = 0; stg < 4; ++stg) {
+        k[stg] = Rk4Stages<R, BX, BY, BZ>::get(blend, stg);
+        nblk[stg] = blocks_for<R>(k[stg], g, smem);
+    }
     // steps n0 .. n0+cnt-1 with stage times relative to the device clock
     auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
         for (int64_t n = 0; n < cnt; ++n) {
             a.t_off = (double)n * p->dt;
             for (int stg = 0; stg < 4; ++stg) {
-                k<<<nblk, th, smem, cs>>>(a, G, stg);
+                k[stg]<<<nblk[stg], th, smem, cs>>>(a, G);
                 GPE_LAUNCH_CHECK();
             }
         }
