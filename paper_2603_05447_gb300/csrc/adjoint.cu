@@ -74,8 +74,9 @@ __global__ void GPE_BOUNDS(R) k_adj_stage(const AdjArgs<R> a, const GridView G)
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     double dot[1] = {0.0};
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
-        brick_apply<BX, BY, BZ, false>(ws, G, b, a.mu_in, Scale<R>{a.m_scale}, a.ihx2, a.ihy2, a.ihz2,
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
+        brick_apply<BX, BY, BZ, false>(ws, G, b, b + stride < G.nb ? b + stride : -1, a.mu_in, Scale<R>{a.m_scale}, a.ihx2, a.ihy2, a.ihz2,
                                        [&](uint32_t idx, const CT(&M)[4], const CT(&L)[4]) {
             R V0[4], V1[4];
             CT Y[4], lam[4], acc[4];
@@ -191,7 +192,7 @@ struct gpe_tape {
     void *d_ckpt = nullptr;  // [nck * n_packed]
     void *d_seg = nullptr;   // [K * n_packed]
     void *d_lam = nullptr, *d_mu[2] = {nullptr, nullptr}, *d_acc = nullptr;
-    void *d_w[3] = {nullptr, nullptr, nullptr};  // Y2, Y3, Y4
+    void *d_w[4] = {nullptr, nullptr, nullptr, nullptr};  // Y2, Y3, Y4, RK4 partial sum
     double *d_grad = nullptr;
     double *d_clock = nullptr;
     RedScratch red;
@@ -206,7 +207,7 @@ static void tape_free(gpe_tape *t)
     dev_free(t->d_mu[0]);
     dev_free(t->d_mu[1]);
     dev_free(t->d_acc);
-    for (int i = 0; i < 3; ++i) dev_free(t->d_w[i]);
+    for (int i = 0; i < 4; ++i) dev_free(t->d_w[i]);
     dev_free(t->d_grad);
     dev_free(t->d_clock);
     red_free(t->red);
@@ -239,7 +240,7 @@ extern "C" int gpe_ramp_forward(gpe_state *st, const gpe_real_params *p, int64_t
     int rc = GPE_OK;
     rc = dev_alloc(&t->d_ckpt, bytes * t->nck);
     if (rc == GPE_OK) rc = dev_alloc(&t->d_seg, bytes * t->K);
-    for (void **b : {&t->d_lam, &t->d_mu[0], &t->d_mu[1], &t->d_acc, &t->d_w[0], &t->d_w[1], &t->d_w[2]})
+    for (void **b : {&t->d_lam, &t->d_mu[0], &t->d_mu[1], &t->d_acc, &t->d_w[0], &t->d_w[1], &t->d_w[2], &t->d_w[3]})
         if (rc == GPE_OK && (rc = dev_alloc(b, bytes)) == GPE_OK) rc = dev_zero(*b, bytes);
     if (rc == GPE_OK) rc = dev_alloc_t(&t->d_grad, GPE_MAX_KNOTS);
     if (rc == GPE_OK) rc = dev_alloc_t(&t->d_clock, 1);
@@ -304,7 +305,8 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
     if (!f.V0 || !f.V1) return fail(GPE_ERR_STATE, "ramp needs potential slots 0 and 1");
     f.y2 = (CT *)t->d_w[0];
     f.y3 = (CT *)t->d_w[1];
-    f.y4 = (CT *)t->d_w[2];
+    f.y4 = (CT *)t->d_w[2];  // kept apart from Y2: the reverse sweep reads all three
+    f.w = (CT *)t->d_w[3];
     f.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
     f.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
     f.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));

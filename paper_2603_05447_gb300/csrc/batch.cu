@@ -55,9 +55,11 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G
     constexpr int NW = KernelCfg<R>::NW;
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
         const ShellParams &P = a.sh[shell_of(G.rec[b])];
         if (P.converged) continue;  // uniform across the warp
+        const int64_t nx = b + stride < G.nb ? b + stride : -1;
         const R g = (R)P.g, dt = (R)P.dt;
         const R ihx2 = (R)P.ihx2, ihy2 = (R)P.ihy2, ihz2 = (R)P.ihz2;
         const R q4 = dt / (R)4, hg = g * dt / (R)2;
@@ -83,14 +85,15 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G
             st4((STAGE == 0 ? a.tmp : a.psi) + idx, o);
         };
         if (STAGE == 0)
-            brick_apply<BX, BY, BZ, false>(ws, G, b, a.psi, DiagLoad<R>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2, body);
+            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.psi, DiagLoad<R>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2, body);
         else
-            brick_apply<BX, BY, BZ, false>(ws, G, b, a.tmp, Identity(), ihx2, ihy2, ihz2, body);
+            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.tmp, Identity(), ihx2, ihy2, ihz2, body);
         if (STAGE == 1) {
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
             if (lane == 0) a.part[b * 5] = acc;
         }
     }
+    cp_async_wait_all();  // a fetched-ahead record row of a skipped brick
 }
 
 // per shell: norm from the brick partials (brick order), next factor
@@ -141,12 +144,14 @@ __global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R> a, const GridView G
     constexpr int NW = KernelCfg<R>::NW;
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
         const ShellParams &P = a.sh[shell_of(G.rec[b])];
         if (P.converged) continue;
+        const int64_t nx = b + stride < G.nb ? b + stride : -1;
         const R g = (R)P.g;
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        brick_apply<BX, BY, BZ, false>(ws, G, b, a.psi, Identity(), (R)P.ihx2, (R)P.ihy2, (R)P.ihz2,
+        brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.psi, Identity(), (R)P.ihx2, (R)P.ihy2, (R)P.ihz2,
                                        [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
             R V[4];
             ldr4(a.V + idx, V);
@@ -168,6 +173,7 @@ __global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R> a, const GridView G
             if (lane == 0) a.part[b * 5 + k] = x;
         }
     }
+    cp_async_wait_all();  // a fetched-ahead record row of a skipped brick
 }
 
 // per shell: observables from the brick partials, then the convergence test

@@ -152,17 +152,6 @@ struct Identity {
     __device__ __forceinline__ CT operator()(CT v, uint32_t) const { return v; }
 };
 
-// Records of brick b (slot 0) and of its six face neighbours (slots 1..6,
-// order -x +x -y +y -z +z; an absent neighbour has an empty record): one
-// coalesced 224-byte load by 14 lanes into the warp's shared-memory slots.
-__device__ __forceinline__ void load_recs(BrickRec *R, const GridView &G, int64_t b)
-{
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
-    if (lane < 14) reinterpret_cast<uint4 *>(R)[lane] = __ldg(reinterpret_cast<const uint4 *>(G.rec7 + 7 * b) + lane);
-    __syncwarp();
-}
-
 template <bool CG, typename CT>
 __device__ __forceinline__ CT ld1(const CT *p)
 {
@@ -175,7 +164,8 @@ __device__ __forceinline__ CT ld1(const CT *p)
 // take consecutive segments touch consecutive 16-byte units (no shared-memory
 // bank conflicts).  The x face halos are separate columns.  Then the records
 // of the brick and its six face neighbours and the brick's stored segments in
-// order.
+// order.  The records of the warp's next brick are fetched into nrec while
+// the current brick is processed.
 template <typename CT, int BX, int BY, int BZ>
 struct WarpSpace {
     static constexpr int SX = BX / 4, TY = BY + 2, TZ = BZ + 2;
@@ -190,8 +180,10 @@ struct WarpSpace {
     CT xlo[BY * BZ];  // x = -1
     CT xhi[BY * BZ];  // x = BX
     BrickRec rec[7];
+    BrickRec nrec[7];  // records of the warp's next brick, fetched ahead
+    long long nrec_b;  // brick whose records nrec holds (-1: none)
     uint8_t list[NSEG];
-    uint8_t pad[(16 - (NSEG % 16)) % 16];
+    uint8_t pad[(16 - ((NSEG + 8) % 16)) % 16];
 
     __device__ __forceinline__ void get(int s, CT (&v)[4]) const
     {
@@ -230,11 +222,16 @@ constexpr size_t smem_bytes()
     return (size_t)KernelCfg<R>::NW * sizeof(WarpSpace<typename Cx<R>::T, BX, BY, BZ>);
 }
 
+// the calling warp's workspace (call once per kernel: it resets the
+// next-record tag)
 template <typename R, int BX, int BY, int BZ>
 __device__ __forceinline__ WarpSpace<typename Cx<R>::T, BX, BY, BZ> &warp_space()
 {
     extern __shared__ __align__(16) unsigned char gpe_smem[];
-    return reinterpret_cast<WarpSpace<typename Cx<R>::T, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
+    auto &ws = reinterpret_cast<WarpSpace<typename Cx<R>::T, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) == 0) ws.nrec_b = -1;
+    __syncwarp();
+    return ws;
 }
 
 template <typename CT>
@@ -258,13 +255,38 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Records of brick b (slot 0) and of its six face neighbours (slots 1..6,
+// order -x +x -y +y -z +z; an absent neighbour has an empty record) into
+// ws.rec, one 224-byte row of rec7 moved by 14 lanes: from ws.nrec when it
+// was fetched ahead, else from global memory.  Then the row of brick `next`
+// (if >= 0) is fetched ahead into ws.nrec by cp.async; it completes with the
+// tile's copies.
+template <typename WS>
+__device__ __forceinline__ void fetch_recs(WS &ws, const GridView &G, int64_t b, int64_t next)
+{
+    const int lane = threadIdx.x & 31;
+    cp_async_wait_all();
+    __syncwarp();
+    const bool ahead = ws.nrec_b == (long long)b;
+    if (lane < 14)
+        reinterpret_cast<uint4 *>(ws.rec)[lane] = ahead ? reinterpret_cast<const uint4 *>(ws.nrec)[lane]
+                                                        : __ldg(reinterpret_cast<const uint4 *>(G.rec7 + 7 * b) + lane);
+    __syncwarp();
+    if (next >= 0 && lane < 14)
+        cp_async16(reinterpret_cast<uint4 *>(ws.nrec) + lane, reinterpret_cast<const uint4 *>(G.rec7 + 7 * next) + lane,
+                   true);
+    if (lane == 0) ws.nrec_b = next;
+    __syncwarp();
+}
+
 // no operands to prefetch
 struct NoPre {
     struct P {};
     __device__ __forceinline__ P operator()(uint32_t) const { return P{}; }
 };
 
-// Apply body(idx, pre, c, L) to every stored segment of brick b, one warp:
+// Apply body(idx, pre, c, L) to every stored segment of brick b, one warp
+// (next: the brick the warp takes after b, or -1):
 // idx is the packed index of the segment's first cell, pre what load(idx)
 // returned for it, c[4] its values and L[4] their 7-point Laplacians
 // (Eq. (B1)), all taken from src after xf(value, packed index).  The warp
@@ -273,17 +295,17 @@ struct NoPre {
 // zero.  Lanes then take the stored segments in order, so the packed indices
 // of a warp's segments are consecutive and the bodies' own-cell loads and
 // stores coalesce.  The first 32 segments' operands are loaded while the tile
-// is in flight.  With xf the identity the tile is filled by cp.async;
+// is in flight, the next 32's while a group is computed.  With xf the identity the tile is filled by cp.async;
 // otherwise through registers, where xf is applied.
 template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename LOAD, typename BODY>
-__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b,
+__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b, int64_t next,
                                             const CT *src, XF xf, R ihx2, R ihy2, R ihz2, LOAD load, BODY body)
 {
     using S = Seg<BX, BY, BZ>;
     using W = WarpSpace<CT, BX, BY, BZ>;
     constexpr bool ASYNC = std::is_same<XF, Identity>::value;
     const int lane = threadIdx.x & 31;
-    load_recs(ws.rec, G, b);
+    fetch_recs(ws, G, b, next);
     const BrickRec &R0 = ws.rec[0];
     const int nst = __popc(R0.m[0]) + __popc(R0.m[1]) + __popc(R0.m[2]) + __popc(R0.m[3]);
     // one segment (4 cells) into tile slot sl
@@ -348,7 +370,7 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         }
         (face == 0 ? ws.xlo : ws.xhi)[W::h(y, z)] = v;
     }
-    if constexpr (ASYNC) cp_async_wait_all();
+    cp_async_wait_all();
     __syncwarp();
     // stored segments: Laplacian from the tile, then the body
     auto segment = [&](int r, const auto &pre) {
@@ -374,16 +396,22 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         }
         body(R0.off + 4u * (uint32_t)r, pre, c, L);
     };
-    if (lane < nst) segment(lane, p0);
-    for (int r = lane + 32; r < nst; r += 32) segment(r, load(R0.off + 4u * (uint32_t)r));
+    // each iteration loads the operands of the next before computing its own
+    auto cur = p0;
+    for (int r = lane; r < nst; r += 32) {
+        decltype(p0) nxt{};
+        if (r + 32 < nst) nxt = load(R0.off + 4u * (uint32_t)(r + 32));
+        segment(r, cur);
+        cur = nxt;
+    }
 }
 
 // the same without prefetched operands: body(idx, c, L)
 template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename BODY>
-__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b,
+__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b, int64_t next,
                                             const CT *src, XF xf, R ihx2, R ihy2, R ihz2, BODY body)
 {
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, src, xf, ihx2, ihy2, ihz2, NoPre(),
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, src, xf, ihx2, ihy2, ihz2, NoPre(),
                                 [&](uint32_t idx, const NoPre::P &, const CT(&c)[4], const CT(&L)[4]) {
                                     body(idx, c, L);
                                 });
@@ -462,12 +490,16 @@ __device__ __forceinline__ double block_sum(double x)
 // ------------------------------------------------------------ RK4 stages
 // Memory-optimised RK4 (App. A, RK4 a* and b*): the stage states are stored
 // instead of the k_i, so stage i reads only the state it differentiates (with
-// halo) plus the own-cell values of earlier states:
+// halo) plus own-cell values:
 //   stage 0: y2 = y0 + dt/2 f(t, y0)
-//   stage 1: y3 = y0 + dt/2 f(t + dt/2, y2)
+//   stage 1: y3 = y0 + dt/2 f(t + dt/2, y2),  w = -y0 + y2 + 2 y3
 //   stage 2: y4 = y0 + dt   f(t + dt/2, y3)
-//   stage 3: y1 = (-y0 + y2 + 2 y3 + y4)/3 + dt/6 f(t + dt, y4)  (in place of y0)
-// with f(t, y) = -i [ -1/2 lap y + (V(t) + g|y|^2) y ]  (Eq. (8)).
+//   stage 3: y1 = (w + y4)/3 + dt/6 f(t + dt, y4)  (in place of y0)
+// with f(t, y) = -i [ -1/2 lap y + (V(t) + g|y|^2) y ]  (Eq. (8)).  The
+// partial sum w is formed in stage 1, where y0, y2 and y3 are at hand, in the
+// same operation order as the stage-3 combination (-y0 + y2 + 2 y3 + y4)/3:
+// stage 3 then reads one state instead of three.  y4 may share y2's buffer
+// (y2 has no reader after stage 1).
 template <typename R>
 struct RkArgs {
     using CT = typename Cx<R>::T;
@@ -475,6 +507,7 @@ struct RkArgs {
     CT *y2;
     CT *y3;
     CT *y4;
+    CT *w;
     const R *V0;
     const R *V1;
     R ihx2, ihy2, ihz2, g, dt;
@@ -495,37 +528,35 @@ __device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
 // group of 32.  The stage is a template argument so that each stage keeps
 // only its own prefetched operands in registers.
 template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG, int st>
-__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int64_t b,
+__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int64_t b, int64_t next,
                                           WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R s)
 {
     using CT = typename Cx<R>::T;
     const CT *yin = st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4;
     CT *yout = st == 0 ? a.y2 : st == 1 ? a.y3 : st == 2 ? a.y4 : a.y0;
     const R k = (st == 2) ? a.dt : (st == 3 ? a.dt / (R)6 : a.dt / (R)2);
-    constexpr int NV = BLEND ? 4 : 1, NY0 = st > 0 ? 4 : 1, NY23 = st == 3 ? 4 : 1;
+    constexpr int NV = BLEND ? 4 : 1;
     struct P {
         R V0[4], V1[NV];
-        CT y0[NY0], y2[NY23], y3[NY23];
+        CT y[4];  // y0 (stages 1, 2) or w (stage 3)
     };
     auto load = [&](uint32_t idx) {
         P p;
         ldr4(a.V0 + idx, p.V0);
         if constexpr (BLEND) ldr4(a.V1 + idx, p.V1);
-        if constexpr (st > 0) ld4<CG>(a.y0 + idx, p.y0);
-        if constexpr (st == 3) {
-            ld4<CG>(a.y2 + idx, p.y2);
-            ld4<CG>(a.y3 + idx, p.y3);
-        }
+        if constexpr (st == 1 || st == 2) ld4<CG>(a.y0 + idx, p.y);
+        if constexpr (st == 3) ld4<CG>(a.w + idx, p.y);
         return p;
     };
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, yin, Identity(), a.ihx2, a.ihy2, a.ihz2, load,
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, yin, Identity(), a.ihx2, a.ihy2, a.ihz2, load,
                                 [&](uint32_t idx, const P &p, const CT(&c)[4], const CT(&L)[4]) {
         const R(&V0)[4] = p.V0;
-        CT o[4];
+        CT o[4], wv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (!(V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
                 o[i] = czero<CT>();
+                wv[i] = czero<CT>();
                 continue;
             }
             R V = V0[i];
@@ -538,13 +569,18 @@ __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G,
                 o[i].x = c[i].x + k * hi;
                 o[i].y = c[i].y - k * hr;
             } else if constexpr (st < 3) {
-                o[i].x = p.y0[i].x + k * hi;
-                o[i].y = p.y0[i].y - k * hr;
+                o[i].x = p.y[i].x + k * hi;
+                o[i].y = p.y[i].y - k * hr;
+                if constexpr (st == 1) {
+                    wv[i].x = -p.y[i].x + c[i].x + (R)2 * o[i].x;
+                    wv[i].y = -p.y[i].y + c[i].y + (R)2 * o[i].y;
+                }
             } else {
-                o[i].x = (-p.y0[i].x + p.y2[i].x + (R)2 * p.y3[i].x + c[i].x) / (R)3 + k * hi;
-                o[i].y = (-p.y0[i].y + p.y2[i].y + (R)2 * p.y3[i].y + c[i].y) / (R)3 - k * hr;
+                o[i].x = (p.y[i].x + c[i].x) / (R)3 + k * hi;
+                o[i].y = (p.y[i].y + c[i].y) / (R)3 - k * hr;
             }
         }
+        if constexpr (st == 1) st4(a.w + idx, wv);
         st4(yout + idx, o);
     });
 }
@@ -556,8 +592,9 @@ __global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G)
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     const R s = stage_s<R, BLEND>(a, ST);
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
-        rk4_brick<R, BX, BY, BZ, BLEND, false, ST>(a, G, b, ws, s);
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride)
+        rk4_brick<R, BX, BY, BZ, BLEND, false, ST>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, s);
 }
 
 // the four stage kernels of one shape, static (BLEND false) or blended

@@ -214,20 +214,22 @@ __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, co
         const int64_t b0 = (int64_t)c * w.cb;
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
         for (int64_t b = b0 + warp; b < b1; b += NW) {
+            const int64_t nx = b + NW < b1 ? b + NW : -1;
             switch (st) {
-            case 0: rk4_brick<R, BX, BY, BZ, BLEND, true, 0>(a, G, b, ws, s[0]); break;
-            case 1: rk4_brick<R, BX, BY, BZ, BLEND, true, 1>(a, G, b, ws, s[1]); break;
-            case 2: rk4_brick<R, BX, BY, BZ, BLEND, true, 2>(a, G, b, ws, s[2]); break;
-            default: rk4_brick<R, BX, BY, BZ, BLEND, true, 3>(a, G, b, ws, s[3]); break;
+            case 0: rk4_brick<R, BX, BY, BZ, BLEND, true, 0>(a, G, b, nx, ws, s[0]); break;
+            case 1: rk4_brick<R, BX, BY, BZ, BLEND, true, 1>(a, G, b, nx, ws, s[1]); break;
+            case 2: rk4_brick<R, BX, BY, BZ, BLEND, true, 2>(a, G, b, nx, ws, s[2]); break;
+            default: rk4_brick<R, BX, BY, BZ, BLEND, true, 3>(a, G, b, nx, ws, s[3]); break;
             }
         }
         publish(w, st, c);
         if (st == 3) {
-            // y2 and y3 of this chunk have no reader left in this step
+            // y3 and w of this chunk have no reader left in this step (y4,
+            // in y2's buffer, is still read by the neighbour chunks' stage 3)
             const uint32_t p0 = __ldg(&G.rec[b0].off);
             const uint32_t p1 = b1 < G.nb ? __ldg(&G.rec[b1].off) : w.n_packed;
-            discard_range(a.y2 + p0, (size_t)(p1 - p0) * sizeof(CT));
             discard_range(a.y3 + p0, (size_t)(p1 - p0) * sizeof(CT));
+            discard_range(a.w + p0, (size_t)(p1 - p0) * sizeof(CT));
         }
     }
 }
@@ -254,13 +256,13 @@ struct ItpArgs {
 };
 
 template <typename R, int BX, int BY, int BZ, bool CG>
-__device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b,
+__device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b, int64_t next,
                                             WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R sc)
 {
     using CT = typename Cx<R>::T;
     const R q4 = a.dt / (R)4;
     const DiagLoad<R> diag{sc, a.g * a.dt / (R)2, a.E};
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, a.psi, diag, a.ihx2, a.ihy2, a.ihz2,
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.psi, diag, a.ihx2, a.ihy2, a.ihz2,
                                 [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
         R E[4];
         ldr4(a.E + idx, E);
@@ -276,13 +278,13 @@ __device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView 
 }
 
 template <typename R, int BX, int BY, int BZ, bool CG>
-__device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView &G, int64_t b,
+__device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView &G, int64_t b, int64_t next,
                                             WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, double &acc)
 {
     using CT = typename Cx<R>::T;
     const R hg = a.g * a.dt / (R)2;
     const R q4 = a.dt / (R)4;
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2,
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2,
                                 [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
         R E[4];
         ldr4(a.E + idx, E);
@@ -307,8 +309,9 @@ __global__ void GPE_BOUNDS(R) k_itp_a(const ItpArgs<R> a, const GridView G)
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     const R sc = (R)a.scalars[0];
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
-        itp_brick_a<R, BX, BY, BZ, false>(a, G, b, ws, sc);
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride)
+        itp_brick_a<R, BX, BY, BZ, false>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, sc);
 }
 
 template <typename R, int BX, int BY, int BZ>
@@ -318,8 +321,9 @@ __global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, doub
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW)
-        itp_brick_b<R, BX, BY, BZ, false>(a, G, b, ws, acc[0]);
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride)
+        itp_brick_b<R, BX, BY, BZ, false>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, acc[0]);
     double tot[1];
     if (reduce_finish<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         const double nrm = tot[0] * a.dV;
@@ -344,12 +348,14 @@ __global__ void GPE_BOUNDS(R) k_itp_wave(const ItpArgs<R> a, const GridView G, c
         const int64_t b0 = (int64_t)c * w.cb;
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
         if (st == 0) {
-            for (int64_t b = b0 + warp; b < b1; b += NW) itp_brick_a<R, BX, BY, BZ, true>(a, G, b, ws, sc);
+            for (int64_t b = b0 + warp; b < b1; b += NW)
+                itp_brick_a<R, BX, BY, BZ, true>(a, G, b, b + NW < b1 ? b + NW : -1, ws, sc);
             publish(w, st, c);
             continue;
         }
         double acc = 0.0;
-        for (int64_t b = b0 + warp; b < b1; b += NW) itp_brick_b<R, BX, BY, BZ, true>(a, G, b, ws, acc);
+        for (int64_t b = b0 + warp; b < b1; b += NW)
+            itp_brick_b<R, BX, BY, BZ, true>(a, G, b, b + NW < b1 ? b + NW : -1, ws, acc);
         const double part = block_sum(acc);
         if (threadIdx.x == 0) chunk_norm[c] = part;
         publish(w, st, c);
@@ -409,8 +415,9 @@ __global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R> a, const GridView G)
     auto &ws = warp_space<R, BX, BY, BZ>();
     const int warp = threadIdx.x >> 5;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // norm, ekin, epot, eint, nonfinite
-    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += (int64_t)gridDim.x * NW) {
-        brick_apply<BX, BY, BZ, false>(ws, G, b, a.psi, Identity(), a.ihx2, a.ihy2, a.ihz2,
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
+        brick_apply<BX, BY, BZ, false>(ws, G, b, b + stride < G.nb ? b + stride : -1, a.psi, Identity(), a.ihx2, a.ihy2, a.ihz2,
                                        [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
             R V0[4], V1[4];
             ldr4(a.V0 + idx, V0);
@@ -707,7 +714,8 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
     a.y0 = (CT *)st->d_psi;
     a.y2 = (CT *)st->d_work[0];
     a.y3 = (CT *)st->d_work[1];
-    a.y4 = (CT *)st->d_work[2];
+    a.y4 = (CT *)st->d_work[0];  // y2 is dead once stage 1 is done
+    a.w = (CT *)st->d_work[2];
     a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
     a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
     a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
