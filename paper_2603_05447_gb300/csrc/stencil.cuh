@@ -101,35 +101,54 @@ __device__ __forceinline__ double2 shfl_xor(double2 v, int d)
     return v;
 }
 
-// 4 consecutive complex values (one segment); CG: read through L2 only
-// (data written by other blocks of the same launch)
+// 4 consecutive complex values (one segment, 32-byte aligned) with 256-bit
+// accesses, so that each lane moves whole 32-byte sectors; CG: read through
+// L2 only (data written by other blocks of the same launch)
 template <bool CG>
 __device__ __forceinline__ void ld4(const float2 *p, float2 (&v)[4])
 {
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-    const float4 a = CG ? __ldcg(q) : q[0], b = CG ? __ldcg(q + 1) : q[1];
-    v[0] = make_float2(a.x, a.y);
-    v[1] = make_float2(a.z, a.w);
-    v[2] = make_float2(b.x, b.y);
-    v[3] = make_float2(b.z, b.w);
+    float a[8];
+    if (CG)
+        asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+                     : "l"(p));
+    else
+        asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+                     : "l"(p));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = make_float2(a[2 * i], a[2 * i + 1]);
 }
 template <bool CG>
 __device__ __forceinline__ void ld4(const double2 *p, double2 (&v)[4])
 {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = CG ? __ldcg(p + i) : p[i];
+    for (int h = 0; h < 2; ++h) {
+        double a0, a1, a2, a3;
+        if (CG)
+            asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
+                         : "=d"(a0), "=d"(a1), "=d"(a2), "=d"(a3) : "l"(p + 2 * h));
+        else
+            asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(a0), "=d"(a1), "=d"(a2), "=d"(a3) : "l"(p + 2 * h));
+        v[2 * h] = make_double2(a0, a1);
+        v[2 * h + 1] = make_double2(a2, a3);
+    }
 }
 __device__ __forceinline__ void st4(float2 *p, const float2 (&v)[4])
 {
-    float4 *q = reinterpret_cast<float4 *>(p);
-    q[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    q[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0].x), "f"(v[0].y), "f"(v[1].x),
+                 "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y)
+                 : "memory");
 }
 __device__ __forceinline__ void st4(double2 *p, const double2 (&v)[4])
 {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) p[i] = v[i];
+    for (int h = 0; h < 2; ++h)
+        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 2 * h), "d"(v[2 * h].x), "d"(v[2 * h].y),
+                     "d"(v[2 * h + 1].x), "d"(v[2 * h + 1].y)
+                     : "memory");
 }
+// 4 consecutive reals (16- or 32-byte aligned), read-only data
 __device__ __forceinline__ void ldr4(const float *p, float (&v)[4])
 {
     const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
@@ -140,11 +159,7 @@ __device__ __forceinline__ void ldr4(const float *p, float (&v)[4])
 }
 __device__ __forceinline__ void ldr4(const double *p, double (&v)[4])
 {
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
+    asm volatile("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
 }
 
 struct Identity {
@@ -171,12 +186,16 @@ struct WarpSpace {
     static constexpr int SX = BX / 4, TY = BY + 2, TZ = BZ + 2;
     static constexpr int NSLOT = SX * TY * TZ;                   // segment slots incl. y/z halos
     static constexpr int UPS = (int)(4 * sizeof(CT) / 16);       // 16-byte units per segment
+    // plane stride (in units) = 4 (UPS 2) or 2 (UPS 4) mod 8: the UPS units of
+    // one segment fall in distinct 16-byte bank groups, so UPS lanes can fill
+    // one segment's units in one conflict-free access
+    static constexpr int PSTR = NSLOT + (((UPS == 2 ? 4 : 2) - NSLOT % 8) + 8) % 8;
     static constexpr int CPU_ = 4 / UPS;                         // cells per unit
     static constexpr int NSEG = Seg<BX, BY, BZ>::NSEG;
     static constexpr int ROW = SX, PLANE = SX * TY;              // slot strides in y and z
     __device__ __forceinline__ static int slot(int hx, int y, int z) { return hx + SX * ((y + 1) + TY * (z + 1)); }
     __device__ __forceinline__ static int h(int y, int z) { return y + BY * z; }
-    uint4 units[UPS][NSLOT];
+    uint4 units[UPS][PSTR];
     CT xlo[BY * BZ];  // x = -1
     CT xhi[BY * BZ];  // x = BX
     BrickRec rec[7];
@@ -308,14 +327,13 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
     fetch_recs(ws, G, b, next);
     const BrickRec &R0 = ws.rec[0];
     const int nst = __popc(R0.m[0]) + __popc(R0.m[1]) + __popc(R0.m[2]) + __popc(R0.m[3]);
-    // one segment (4 cells) into tile slot sl
-    auto seg_to = [&](const BrickRec &r, int q, int sl) {
+    // unit u of one segment (4 cells; all units when u < 0) into tile slot sl
+    auto seg_to = [&](const BrickRec &r, int q, int sl, int u) {
         uint32_t j = 0;
         const bool ok = seg_index(r, q, j);
         if constexpr (ASYNC) {
             const char *g = reinterpret_cast<const char *>(src + (ok ? j : 0u));
-#pragma unroll
-            for (int u = 0; u < W::UPS; ++u) cp_async16(&ws.units[u][sl], g + 16 * u, ok);
+            cp_async16(&ws.units[u][sl], g + 16 * u, ok);
         } else {
             CT v[4];
             if (ok) {
@@ -329,30 +347,38 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
             ws.put(sl, v);
         }
     };
+    // ASYNC: UPS lanes per segment; else one lane per segment (u ignored)
+    constexpr int LPS = ASYNC ? W::UPS : 1;
     // interior: stored segments from the packed run, zeros elsewhere
+#pragma unroll
+    for (int t = lane; t < S::NSEG * LPS; t += 32) {
+        const int q = t / LPS;
+        seg_to(R0, q, W::slot(q % S::SX, (q / S::SX) % BY, q / S::PLANE), t % LPS);
+    }
+    // the stored segments in order
     int nl = 0;
 #pragma unroll
     for (int it = 0; it < S::NIT; ++it) {
         const int q = it * 32 + lane;
-        const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-        seg_to(R0, q, W::slot(hx, y, z));
         const bool stored = (R0.m[q >> 5] >> (q & 31)) & 1u;
         const unsigned bal = __ballot_sync(0xffffffffu, stored);
         if (stored) ws.list[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
         nl += __popc(bal);
     }
     // -z / +z faces: whole segments of the neighbours' boundary planes
-    for (int u = lane; u < 2 * S::PLANE; u += 32) {
-        const int face = u / S::PLANE, qc = u % S::PLANE;
+#pragma unroll
+    for (int t = lane; t < 2 * S::PLANE * LPS; t += 32) {
+        const int u = t / LPS, face = u / S::PLANE, qc = u % S::PLANE;
         seg_to(ws.rec[5 + face], face == 0 ? qc + S::PLANE * (BZ - 1) : qc,
-               W::slot(qc % S::SX, qc / S::SX, face == 0 ? -1 : BZ));
+               W::slot(qc % S::SX, qc / S::SX, face == 0 ? -1 : BZ), t % LPS);
     }
     // -y / +y faces: segments of the neighbours' boundary rows
-    for (int u = lane; u < 2 * S::SX * BZ; u += 32) {
-        const int face = u / (S::SX * BZ), v_ = u % (S::SX * BZ);
+#pragma unroll
+    for (int t = lane; t < 2 * S::SX * BZ * LPS; t += 32) {
+        const int u = t / LPS, face = u / (S::SX * BZ), v_ = u % (S::SX * BZ);
         const int hx = v_ % S::SX, z = v_ / S::SX;
         seg_to(ws.rec[3 + face], hx + S::SX * (face == 0 ? BY - 1 : 0) + S::PLANE * z,
-               W::slot(hx, face == 0 ? -1 : BY, z));
+               W::slot(hx, face == 0 ? -1 : BY, z), t % LPS);
     }
     // operands of the first 32 stored segments, while the tile is in flight
     typename std::decay<decltype(load(0u))>::type p0{};
