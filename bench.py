@@ -112,7 +112,7 @@ def shell_workload():
     return getattr(inputs, WORKLOADS[_workload_name])
 
 
-def build_grid(gpe, wl, brick=(8, 8, 8), sched=0, chunk=0):
+def build_grid(gpe, wl, brick=(8, 8, 4), sched=0, chunk=0):
     b = wl.box
     gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
     pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
@@ -539,7 +539,7 @@ def main():
                     help="device-resident complex64 timing only (for profiling runs)")
     ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront")
     ap.add_argument("--chunk", type=int, default=0, help="bricks per wavefront task (0: default)")
-    ap.add_argument("--brick", type=int, nargs=3, default=[8, 8, 8])
+    ap.add_argument("--brick", type=int, nargs=3, default=[8, 8, 4])
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64", help="state type of a --quick run")
     args = ap.parse_args()
     global _workload_name

@@ -273,10 +273,10 @@ extern "C" int gpe_ramp_forward(gpe_state *st, const gpe_real_params *p, int64_t
 namespace gpe {
 
 template <typename R, typename K>
-static int adj_blocks(K kernel, const gpe_grid *g, size_t smem)
+static int adj_blocks(K kernel, const gpe_grid *g, size_t smem, int nw = KernelCfg<R>::NW)
 {
-    const int per = prepare_kernel(kernel, KernelCfg<R>::THREADS, smem);
-    const int64_t need = (g->nb + KernelCfg<R>::NW - 1) / KernelCfg<R>::NW;
+    const int per = prepare_kernel(kernel, 32 * nw, smem);
+    const int64_t need = (g->nb + nw - 1) / nw;
     return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->nsm * per, need));
 }
 
@@ -317,14 +317,15 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
     f.ramp.T = p.T_ramp;
     f.ramp.n_knots = p.n_knots;
     for (int k = 0; k < GPE_MAX_KNOTS; ++k) f.ramp.knots[k] = p.knots[k];
-    typename Rk4Stages<R, BX, BY, BZ>::K kf[4];
+    using RS = Rk4Stages<R, BX, BY, BZ>;
+    typename RS::K kf[4];
     auto ka = k_adj_stage<R, BX, BY, BZ, true>;
     const size_t smem = smem_bytes<R, BX, BY, BZ>();
     const int th = KernelCfg<R>::THREADS;
     int nbf[4];
     for (int stg = 0; stg < 4; ++stg) {
-        kf[stg] = Rk4Stages<R, BX, BY, BZ>::get(true, stg);
-        nbf[stg] = adj_blocks<R>(kf[stg], g, smem);
+        kf[stg] = RS::get(true, stg);
+        nbf[stg] = adj_blocks<R>(kf[stg], g, RS::smem(), RS::NW);
     }
     const int nba = adj_blocks<R>(ka, g, smem);
     AdjArgs<R> a{};
@@ -351,7 +352,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
             f.y0 = seg + (m + 1) * np;
             f.t_off = t->t0 + (double)(j * t->K + m) * p.dt;
             for (int stg = 0; stg < 4; ++stg) {
-                kf[stg]<<<nbf[stg], th, smem, s>>>(f, G);
+                kf[stg]<<<nbf[stg], RS::THREADS, RS::smem(), s>>>(f, G);
                 GPE_LAUNCH_CHECK();
             }
         }
@@ -360,7 +361,7 @@ static int backward_impl(gpe_tape *t, const gpe_state *target, double *grad, dou
             f.y0 = seg + m * np;
             f.t_off = tm;
             for (int stg = 0; stg < 3; ++stg) {  // Y2, Y3, Y4
-                kf[stg]<<<nbf[stg], th, smem, s>>>(f, G);
+                kf[stg]<<<nbf[stg], RS::THREADS, RS::smem(), s>>>(f, G);
                 GPE_LAUNCH_CHECK();
             }
             // stages 4, 3, 2, 1 of the reverse sweep

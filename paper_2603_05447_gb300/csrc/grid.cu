@@ -74,7 +74,40 @@ __device__ __forceinline__ void cell_values(const VSource &src, const BoxD &bx, 
     }
 }
 
-// (1) occupancy of every brick-grid position (lexicographic q)
+// Lower bound of an analytic potential over the axis-aligned box
+// [xl,xh] x [yl,yh] x [zl,zh] (true for an unknown kind: no bound).  Both
+// potentials are separable in the squares of the coordinates, so the
+// extremes of each square over an interval give the exact range: the
+// harmonic potential's minimum directly, and for the ellipsoidal shell the
+// range [rmin, rmax] of the scaled radius, from which the minimum of
+// (rho - 1)^2 follows.
+__device__ __forceinline__ bool pot_may_select(const PotDesc &P, double cut, double xl, double xh, double yl,
+                                               double yh, double zl, double zh)
+{
+    auto sqmin = [](double l, double h) { return (l <= 0.0 && h >= 0.0) ? 0.0 : fmin(l * l, h * h); };
+    auto sqmax = [](double l, double h) { return fmax(l * l, h * h); };
+    double vmin;
+    if (P.kind == GPE_POT_HARMONIC) {
+        vmin = 0.5 * (P.p[0] * P.p[0] * sqmin(xl, xh) + P.p[1] * P.p[1] * sqmin(yl, yh) +
+                      P.p[2] * P.p[2] * sqmin(zl, zh));
+    } else if (P.kind == GPE_POT_ELLIPSOID_SHELL) {
+        const double ia = 1.0 / (P.p[1] * P.p[1]), ib = 1.0 / (P.p[2] * P.p[2]), ic = 1.0 / (P.p[3] * P.p[3]);
+        const double rmin = sqrt(sqmin(xl, xh) * ia + sqmin(yl, yh) * ib + sqmin(zl, zh) * ic);
+        const double rmax = sqrt(sqmax(xl, xh) * ia + sqmax(yl, yh) * ib + sqmax(zl, zh) * ic);
+        const double d = (rmin <= 1.0 && rmax >= 1.0) ? 0.0 : fmin(fabs(rmin - 1.0), fabs(rmax - 1.0));
+        vmin = 0.5 * P.p[0] * P.p[0] * d * d;
+    } else {
+        return true;
+    }
+    // the cell test rounds differently: keep a relative margin, so that the
+    // bound only ever lets more bricks through to the exact per-cell test
+    return vmin < cut * (1.0 + 1e-9) + 1e-300;
+}
+
+// (1) occupancy of every brick-grid position (lexicographic q).  Analytic
+// sources first test the brick's cell-centre box against a lower bound of
+// the potential; only bricks that may hold a selected cell are tested cell
+// by cell.
 __global__ void k_occupancy(VSource src, BoxD box, int BX, int BY, int BZ, int64_t nbx,
                             int64_t nby, int64_t nbz, uint8_t *occ)
 {
@@ -82,6 +115,19 @@ __global__ void k_occupancy(VSource src, BoxD box, int BX, int BY, int BZ, int64
     if (q >= nbx * nby * nbz) return;
     const int64_t qx = q % nbx, qy = (q / nbx) % nby, qz = q / (nbx * nby);
     const int BC = BX * BY * BZ;
+    if (src.mode != 0) {
+        const int64_t i0 = qx * BX, j0 = qy * BY, k0 = qz * BZ;
+        const int64_t i1 = min(i0 + BX, box.nx) - 1, j1 = min(j0 + BY, box.ny) - 1, k1 = min(k0 + BZ, box.nz) - 1;
+        const double xl = box.x0 + i0 * box.hx, xh = box.x0 + i1 * box.hx;
+        const double yl = box.y0 + j0 * box.hy, yh = box.y0 + j1 * box.hy;
+        const double zl = box.z0 + k0 * box.hz, zh = box.z0 + k1 * box.hz;
+        bool may = pot_may_select(src.p0, src.cut0, xl, xh, yl, yh, zl, zh);
+        if (src.mode == 2) may = may || pot_may_select(src.p1, src.cut1, xl, xh, yl, yh, zl, zh);
+        if (!may) {  // uniform across the block
+            if (threadIdx.x == 0) occ[q] = 0;
+            return;
+        }
+    }
     int sel_any = 0;
     for (int l = threadIdx.x; l < BC; l += blockDim.x) {
         int64_t i = qx * BX + l % BX, j = qy * BY + (l / BX) % BY, k = qz * BZ + l / (BX * BY);

@@ -13,20 +13,30 @@ namespace gpe {
 // Stencil kernels run one brick per warp; a block holds NW warps, each with
 // its own shared-memory workspace (brick tile with face halo, the 7 brick
 // records and the list of stored segments), passed as dynamic shared memory.
+#ifndef GPE_NW_F
+#define GPE_NW_F 8
+#endif
+// fetch the records of a warp's next brick while it processes the current one
+#ifndef GPE_REC_AHEAD
+#define GPE_REC_AHEAD 1
+#endif
 template <typename R>
 struct KernelCfg {
-    static constexpr int NW = sizeof(R) == 4 ? 8 : 4;  // warps per block
+    static constexpr int NW = sizeof(R) == 4 ? GPE_NW_F : 4;  // warps per block
     static constexpr int THREADS = 32 * NW;
 };
 
-// Minimum resident blocks per SM requested from the register allocator.
+// Minimum resident blocks per SM requested from the register allocator:
+// as many as the shared-memory workspaces allow (228 KiB per SM, 1 KiB
+// reserved per block), at most GPE_MINB_F (single precision) / GPE_MINB_D
+// (double precision, whose kernels need more registers).
 #ifndef GPE_MINB_F
-#define GPE_MINB_F 3
+#define GPE_MINB_F 4
 #endif
 #ifndef GPE_MINB_D
 #define GPE_MINB_D 3
 #endif
-#define GPE_BOUNDS(R) __launch_bounds__(KernelCfg<R>::THREADS, (sizeof(R) == 4 ? GPE_MINB_F : GPE_MINB_D))
+#define GPE_BOUNDS(R) __launch_bounds__(KernelCfg<R>::THREADS, (min_blocks<R, BX, BY, BZ>()))
 
 // ------------------------------------------------------------ packed layout
 // supported brick shapes (shape id, BX, BY, BZ)
@@ -179,7 +189,7 @@ __device__ __forceinline__ CT ld1(const CT *p)
 // take consecutive segments touch consecutive 16-byte units (no shared-memory
 // bank conflicts).  The x face halos are separate columns.  Then the records
 // of the brick and its six face neighbours and the brick's stored segments in
-// order.  The records of the warp's next brick are fetched into nrec while
+// order, each as its tile slot and x-halo row (slot | h << 8).  The records of the warp's next brick are fetched into nrec while
 // the current brick is processed.
 template <typename CT, int BX, int BY, int BZ>
 struct WarpSpace {
@@ -199,10 +209,15 @@ struct WarpSpace {
     CT xlo[BY * BZ];  // x = -1
     CT xhi[BY * BZ];  // x = BX
     BrickRec rec[7];
+#if GPE_REC_AHEAD
     BrickRec nrec[7];  // records of the warp's next brick, fetched ahead
     long long nrec_b;  // brick whose records nrec holds (-1: none)
-    uint8_t list[NSEG];
-    uint8_t pad[(16 - ((NSEG + 8) % 16)) % 16];
+    uint16_t list[NSEG];
+    uint8_t pad[(16 - ((2 * NSEG + 8) % 16)) % 16];
+#else
+    uint16_t list[NSEG];
+    uint8_t pad[(16 - ((2 * NSEG) % 16)) % 16];
+#endif
 
     __device__ __forceinline__ void get(int s, CT (&v)[4]) const
     {
@@ -244,12 +259,22 @@ constexpr size_t smem_bytes()
 // the calling warp's workspace (call once per kernel: it resets the
 // next-record tag)
 template <typename R, int BX, int BY, int BZ>
+constexpr int min_blocks()
+{
+    const int cap = sizeof(R) == 4 ? GPE_MINB_F : GPE_MINB_D;
+    const int fit = (int)((228u * 1024u) / (smem_bytes<R, BX, BY, BZ>() + 1024u));
+    return fit < 1 ? 1 : (fit < cap ? fit : cap);
+}
+
+template <typename R, int BX, int BY, int BZ>
 __device__ __forceinline__ WarpSpace<typename Cx<R>::T, BX, BY, BZ> &warp_space()
 {
     extern __shared__ __align__(16) unsigned char gpe_smem[];
     auto &ws = reinterpret_cast<WarpSpace<typename Cx<R>::T, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
+#if GPE_REC_AHEAD
     if ((threadIdx.x & 31) == 0) ws.nrec_b = -1;
     __syncwarp();
+#endif
     return ws;
 }
 
@@ -286,6 +311,7 @@ __device__ __forceinline__ void fetch_recs(WS &ws, const GridView &G, int64_t b,
     const int lane = threadIdx.x & 31;
     cp_async_wait_all();
     __syncwarp();
+#if GPE_REC_AHEAD
     const bool ahead = ws.nrec_b == (long long)b;
     if (lane < 14)
         reinterpret_cast<uint4 *>(ws.rec)[lane] = ahead ? reinterpret_cast<const uint4 *>(ws.nrec)[lane]
@@ -296,6 +322,11 @@ __device__ __forceinline__ void fetch_recs(WS &ws, const GridView &G, int64_t b,
                    true);
     if (lane == 0) ws.nrec_b = next;
     __syncwarp();
+#else
+    (void)next;
+    if (lane < 14) reinterpret_cast<uint4 *>(ws.rec)[lane] = __ldg(reinterpret_cast<const uint4 *>(G.rec7 + 7 * b) + lane);
+    __syncwarp();
+#endif
 }
 
 // no operands to prefetch
@@ -349,21 +380,35 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
     };
     // ASYNC: UPS lanes per segment; else one lane per segment (u ignored)
     constexpr int LPS = ASYNC ? W::UPS : 1;
-    // interior: stored segments from the packed run, zeros elsewhere
-#pragma unroll
-    for (int t = lane; t < S::NSEG * LPS; t += 32) {
-        const int q = t / LPS;
-        seg_to(R0, q, W::slot(q % S::SX, (q / S::SX) % BY, q / S::PLANE), t % LPS);
-    }
-    // the stored segments in order
+    // the stored segments in order (tile slot, x-halo row); with ASYNC the
+    // unstored interior slots are zeroed here
     int nl = 0;
 #pragma unroll
     for (int it = 0; it < S::NIT; ++it) {
         const int q = it * 32 + lane;
+        const int y = (q / S::SX) % BY, z = q / S::PLANE;
+        const int sl = W::slot(q % S::SX, y, z);
         const bool stored = (R0.m[q >> 5] >> (q & 31)) & 1u;
         const unsigned bal = __ballot_sync(0xffffffffu, stored);
-        if (stored) ws.list[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
+        if (stored) {
+            ws.list[nl + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(sl | (W::h(y, z) << 8));
+        } else if constexpr (ASYNC) {
+#pragma unroll
+            for (int u = 0; u < W::UPS; ++u) ws.units[u][sl] = make_uint4(0, 0, 0, 0);
+        }
         nl += __popc(bal);
+    }
+    // interior
+    if constexpr (ASYNC) {
+        // stored segments along the packed run: UPS lanes per segment, each
+        // one contiguous 16-byte unit
+        __syncwarp();
+        const char *run = reinterpret_cast<const char *>(src + R0.off);
+        for (int t = lane; t < nl * W::UPS; t += 32)
+            cp_async16(&ws.units[t % W::UPS][ws.list[t / W::UPS] & 0xff], run + 16 * t, true);
+    } else {
+#pragma unroll
+        for (int q = lane; q < S::NSEG; q += 32) seg_to(R0, q, W::slot(q % S::SX, (q / S::SX) % BY, q / S::PLANE), 0);
     }
     // -z / +z faces: whole segments of the neighbours' boundary planes
 #pragma unroll
@@ -398,27 +443,27 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
     }
     cp_async_wait_all();
     __syncwarp();
-    // stored segments: Laplacian from the tile, then the body
+    // stored segments: Laplacian from the tile, then the body.  Opposite
+    // neighbours are summed first and the centre term enters once:
+    // L = (x- + x+) / hx^2 + (y- + y+) / hy^2 + (z- + z+) / hz^2 - c6 c.
+    const R c6 = (R)2 * (ihx2 + ihy2 + ihz2);
     auto segment = [&](int r, const auto &pre) {
-        const int q = ws.list[r];
-        const int hx = q % S::SX, y = (q / S::SX) % BY, z = q / S::PLANE;
-        const int sl = W::slot(hx, y, z);
+        const int e = ws.list[r];
+        const int sl = e & 0xff, hrow = e >> 8, hx = sl % S::SX;
         CT c[4], ym[4], yp[4], zm[4], zp[4], L[4];
         ws.get(sl, c);
         ws.get(sl - W::ROW, ym);
         ws.get(sl + W::ROW, yp);
         ws.get(sl - W::PLANE, zm);
         ws.get(sl + W::PLANE, zp);
-        const CT xm = hx == 0 ? ws.xlo[W::h(y, z)] : ws.last(sl - 1);
-        const CT xp = hx == S::SX - 1 ? ws.xhi[W::h(y, z)] : ws.first(sl + 1);
+        const CT xm = hx == 0 ? ws.xlo[hrow] : ws.last(sl - 1);
+        const CT xp = hx == S::SX - 1 ? ws.xhi[hrow] : ws.first(sl + 1);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const CT l = i == 0 ? xm : c[i - 1];
             const CT rr = i == 3 ? xp : c[i + 1];
-            L[i].x = (rr.x - 2 * c[i].x + l.x) * ihx2 + (yp[i].x - 2 * c[i].x + ym[i].x) * ihy2 +
-                     (zp[i].x - 2 * c[i].x + zm[i].x) * ihz2;
-            L[i].y = (rr.y - 2 * c[i].y + l.y) * ihx2 + (yp[i].y - 2 * c[i].y + ym[i].y) * ihy2 +
-                     (zp[i].y - 2 * c[i].y + zm[i].y) * ihz2;
+            L[i].x = (rr.x + l.x) * ihx2 + (yp[i].x + ym[i].x) * ihy2 + (zp[i].x + zm[i].x) * ihz2 - c6 * c[i].x;
+            L[i].y = (rr.y + l.y) * ihx2 + (yp[i].y + ym[i].y) * ihy2 + (zp[i].y + zm[i].y) * ihz2 - c6 * c[i].y;
         }
         body(R0.off + 4u * (uint32_t)r, pre, c, L);
     };
@@ -550,43 +595,47 @@ __device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
     return (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + c * a.dtd);
 }
 
-// One RK4 stage (st = 0..3) on brick b, one warp, lane = segment within each
-// group of 32.  The stage is a template argument so that each stage keeps
-// only its own prefetched operands in registers.
-template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG, int st>
-__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int64_t b, int64_t next,
-                                          WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R s)
-{
+// One RK4 stage (st = 0..3): operand loads and the per-segment update.  The
+// stage is a template argument so that each stage keeps only its own
+// prefetched operands in registers.
+template <typename R, bool BLEND, bool CG, int st>
+struct Rk4Body {
     using CT = typename Cx<R>::T;
-    const CT *yin = st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4;
-    CT *yout = st == 0 ? a.y2 : st == 1 ? a.y3 : st == 2 ? a.y4 : a.y0;
-    const R k = (st == 2) ? a.dt : (st == 3 ? a.dt / (R)6 : a.dt / (R)2);
-    constexpr int NV = BLEND ? 4 : 1;
+    static constexpr int NV = BLEND ? 4 : 1;
     struct P {
         R V0[4], V1[NV];
         CT y[4];  // y0 (stages 1, 2) or w (stage 3)
     };
-    auto load = [&](uint32_t idx) {
+    const RkArgs<R> &a;
+    R s, k;
+    CT *yout;
+    __device__ __forceinline__ Rk4Body(const RkArgs<R> &a_, R s_)
+        : a(a_), s(s_), k(st == 2 ? a_.dt : (st == 3 ? a_.dt / (R)6 : a_.dt / (R)2)),
+          yout(st == 0 ? a_.y2 : st == 1 ? a_.y3 : st == 2 ? a_.y4 : a_.y0)
+    {
+    }
+    __device__ __forceinline__ const CT *yin() const { return st == 0 ? a.y0 : st == 1 ? a.y2 : st == 2 ? a.y3 : a.y4; }
+    __device__ __forceinline__ P load(uint32_t idx) const
+    {
         P p;
         ldr4(a.V0 + idx, p.V0);
         if constexpr (BLEND) ldr4(a.V1 + idx, p.V1);
         if constexpr (st == 1 || st == 2) ld4<CG>(a.y0 + idx, p.y);
         if constexpr (st == 3) ld4<CG>(a.w + idx, p.y);
         return p;
-    };
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, yin, Identity(), a.ihx2, a.ihy2, a.ihz2, load,
-                                [&](uint32_t idx, const P &p, const CT(&c)[4], const CT(&L)[4]) {
-        const R(&V0)[4] = p.V0;
+    }
+    __device__ __forceinline__ void operator()(uint32_t idx, const P &p, const CT (&c)[4], const CT (&L)[4]) const
+    {
         CT o[4], wv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (!(V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
+            if (!(p.V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
                 o[i] = czero<CT>();
                 wv[i] = czero<CT>();
                 continue;
             }
-            R V = V0[i];
-            if constexpr (BLEND) V = ((R)1 - s) * V0[i] + s * p.V1[i];
+            R V = p.V0[i];
+            if constexpr (BLEND) V = ((R)1 - s) * p.V0[i] + s * p.V1[i];
             const R w = V + a.g * (c[i].x * c[i].x + c[i].y * c[i].y);
             const R hr = (R)(-0.5) * L[i].x + w * c[i].x;
             const R hi = (R)(-0.5) * L[i].y + w * c[i].y;
@@ -608,7 +657,18 @@ __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G,
         }
         if constexpr (st == 1) st4(a.w + idx, wv);
         st4(yout + idx, o);
-    });
+    }
+};
+
+// One RK4 stage on brick b, one warp, lane = segment within each group of 32.
+template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG, int st>
+__device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int64_t b, int64_t next,
+                                          WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R s)
+{
+    using B = Rk4Body<R, BLEND, CG, st>;
+    const B body(a, s);
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, body.yin(), Identity(), a.ihx2, a.ihy2, a.ihz2,
+                                [&](uint32_t idx) { return body.load(idx); }, body);
 }
 
 template <typename R, int BX, int BY, int BZ, bool BLEND, int ST>
@@ -623,10 +683,14 @@ __global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G)
         rk4_brick<R, BX, BY, BZ, BLEND, false, ST>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, s);
 }
 
-// the four stage kernels of one shape, static (BLEND false) or blended
+// the four stage kernels of one shape, static (BLEND false) or blended, and
+// their launch shape
 template <typename R, int BX, int BY, int BZ>
 struct Rk4Stages {
     using K = void (*)(RkArgs<R>, GridView);
+    static constexpr int NW = KernelCfg<R>::NW;
+    static constexpr int THREADS = 32 * NW;
+    static constexpr size_t smem() { return smem_bytes<R, BX, BY, BZ>(); }
     static K get(bool blend, int st)
     {
         static const K t[2][4] = {

@@ -80,16 +80,20 @@ static int per_sm_for(K kernel, int threads, size_t smem)
     return per;
 }
 
-// a grid of resident blocks, no more than one warp per brick
-template <typename R, typename K>
-static int blocks_for(K kernel, const gpe_grid *g, size_t smem)
+// a grid of resident blocks of nw warps, no more than one warp per brick
+template <typename K>
+static int blocks_for_nw(K kernel, const gpe_grid *g, size_t smem, int nw)
 {
-    constexpr int NW = KernelCfg<R>::NW;
-    int64_t b = (int64_t)g->nsm * per_sm_for(kernel, KernelCfg<R>::THREADS, smem);
-    const int64_t need = (g->nb + NW - 1) / NW;
+    int64_t b = (int64_t)g->nsm * per_sm_for(kernel, 32 * nw, smem);
+    const int64_t need = (g->nb + nw - 1) / nw;
     if (b > need) b = need;
     if (b < 1) b = 1;
     return (int)b;
+}
+template <typename R, typename K>
+static int blocks_for(K kernel, const gpe_grid *g, size_t smem)
+{
+    return blocks_for_nw(kernel, g, smem, KernelCfg<R>::NW);
 }
 
 // ------------------------------------------------------------ wavefront sync
@@ -745,18 +749,19 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
         }
         return GPE_OK;
     }
-    typename Rk4Stages<R, BX, BY, BZ>::K k[4];
+    using RS = Rk4Stages<R, BX, BY, BZ>;
+    typename RS::K k[4];
     int nblk[4];
     for (int stg = 0; stg < 4; ++stg) {
-        k[stg] = Rk4Stages<R, BX, BY, BZ>::get(blend, stg);
-        nblk[stg] = blocks_for<R>(k[stg], g, smem);
+        k[stg] = RS::get(blend, stg);
+        nblk[stg] = blocks_for_nw(k[stg], g, RS::smem(), RS::NW);
     }
     // steps n0 .. n0+cnt-1 with stage times relative to the device clock
     auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
         for (int64_t n = 0; n < cnt; ++n) {
             a.t_off = (double)n * p->dt;
             for (int stg = 0; stg < 4; ++stg) {
-                k[stg]<<<nblk[stg], th, smem, cs>>>(a, G);
+                k[stg]<<<nblk[stg], RS::THREADS, RS::smem(), cs>>>(a, G);
                 GPE_LAUNCH_CHECK();
             }
         }

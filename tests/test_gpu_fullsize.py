@@ -1,6 +1,6 @@
 """Parity at the headline size, in the launch configuration bench.py times
-(1024^3 shell, ~2.9e7 active cells, 8x8x8 bricks, z-major order, staged
-schedule): one GPU step on the whole grid, then sampled active cells compared
+(1024^3 shell, ~2.9e7 active cells, the bench's brick shape, z-major order,
+staged schedule): one GPU step on the whole grid, then sampled active cells compared
 with the FP64 oracle run on the 11^3 patch around each sample.  One RK4 step
 applies the stencil four times, so a cell's new value depends only on cells
 within 4 of it and the patch (half-width 5) reproduces it exactly.
@@ -44,8 +44,10 @@ def big():
     seg = act.reshape(info.n_bricks, bc // 4, 4).any(axis=2)
     off = 4 * np.concatenate([[0], np.cumsum(seg.sum(axis=1))[:-1]]).astype(np.int64)
     rank = np.cumsum(seg, axis=1) - 1
-    bid = {tuple(c): n for n, c in enumerate(org // 8)}
-    yield dict(wl=wl, grid=grid, psi0=psi0, info=info, act=act, seg=seg, off=off, rank=rank, bid=bid, V=V)
+    shape = np.array([info.bx, info.by, info.bz])
+    bid = {tuple(c): n for n, c in enumerate(org // shape)}
+    yield dict(wl=wl, grid=grid, psi0=psi0, info=info, act=act, seg=seg, off=off, rank=rank, bid=bid, V=V,
+               shape=tuple(int(x) for x in shape))
     gpe.gpe_grid_destroy(grid)
 
 
@@ -58,10 +60,11 @@ def patch(B, i, j, k):
     inside = (I >= 0) & (I < n) & (J >= 0) & (J < n) & (K >= 0) & (K < n)
     for (a, b_, c) in zip(*np.nonzero(inside)):
         ii, jj, kk = I[a, b_, c], J[a, b_, c], K[a, b_, c]
-        b = B["bid"].get((ii // 8, jj // 8, kk // 8))
+        bx, by, bz = B["shape"]
+        b = B["bid"].get((ii // bx, jj // by, kk // bz))
         if b is None:
             continue
-        l = (ii % 8) + 8 * ((jj % 8) + 8 * (kk % 8))
+        l = (ii % bx) + bx * ((jj % by) + by * (kk % bz))
         if B["act"][b, l]:
             idx[a, b_, c] = B["off"][b] + 4 * B["rank"][b, l // 4] + l % 4
     return idx >= 0, idx
@@ -77,7 +80,8 @@ def samples(B, seed):
         if ls.size == 0:
             continue
         l = rng.choice(ls)
-        out.append((org[bb, 0] + l % 8, org[bb, 1] + (l // 8) % 8, org[bb, 2] + l // 64))
+        bx, by, _ = B["shape"]
+        out.append((org[bb, 0] + l % bx, org[bb, 1] + (l // bx) % by, org[bb, 2] + l // (bx * by)))
         if len(out) == NSAMPLE:
             break
     return out

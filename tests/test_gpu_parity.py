@@ -154,6 +154,54 @@ def test_analytic_builder_matches_dense_samples():
         gpe.gpe_grid_destroy(gd)
 
 
+def _builder_cases():
+    shell = inputs.EllipsoidShell(400.0, 1.0, 0.9, 0.8)
+    return {
+        # a box that is not a whole number of bricks on any axis
+        "shell": (inputs.Box(70, 66, 61, 1 / 30, 1 / 30, 1 / 30), [(gpe.GPE_POT_ELLIPSOID_SHELL, shell, 40.0)]),
+        "harmonic": (inputs.Box(41, 36, 45, 0.25, 0.3, 0.2), [(gpe.GPE_POT_HARMONIC, inputs.Harmonic(1.0, 1.3, 0.7), 4.0)]),
+        "blend": (inputs.Box(48, 48, 48, 1 / 20, 1 / 20, 1 / 20),
+                  [(gpe.GPE_POT_ELLIPSOID_SHELL, shell, 30.0),
+                   (gpe.GPE_POT_ELLIPSOID_SHELL, inputs.EllipsoidShell(300.0, 0.7, 0.75, 0.6), 20.0)]),
+    }
+
+
+def _params(kind, pot):
+    if kind == gpe.GPE_POT_HARMONIC:
+        return (pot.wx, pot.wy, pot.wz)
+    return (pot.w, pot.a, pot.b, pot.c)
+
+
+@pytest.mark.parametrize("name", ["shell", "harmonic", "blend"])
+@pytest.mark.parametrize("brick", [(8, 8, 8), (8, 8, 4)])
+def test_analytic_builder_selects_exactly_the_cells_below_the_cut(name, brick):
+    """Every cell with V < V_cut (of either potential for a blend) is active
+    and no other, up to cells within rounding of the cut: the per-brick bound
+    that skips far bricks never drops a selected cell."""
+    box, pots = _builder_cases()[name]
+    gb = gpe.make_box(box.nx, box.ny, box.nz, box.hx, box.hy, box.hz)
+    P = [gpe.make_potential(k, *_params(k, p)) for k, p, _ in pots]
+    opts = gpe.make_opts(brick)
+    if len(pots) == 1:
+        grid = gpe.gpe_grid_create_analytic(gb, P[0], pots[0][2], opts)
+    else:
+        grid = gpe.gpe_grid_create_blend(gb, P[0], pots[0][2], P[1], pots[1][2], opts)
+    try:
+        _, i, j, k = gpe.packed_coords(grid)
+        got = np.zeros(box.shape, bool)
+        got[k, j, i] = True
+        want = np.zeros(box.shape, bool)
+        near = np.zeros(box.shape, bool)
+        for _, p, cut in pots:
+            V = inputs.dense_potential(box, p)
+            want |= V < cut
+            near |= np.abs(V - cut) <= 1e-9 * cut
+        assert want.any()
+        assert not np.any((got != want) & ~near)
+    finally:
+        gpe.gpe_grid_destroy(grid)
+
+
 def test_empty_region_and_destroy_order_errors():
     case = single_cell()
     with pytest.raises(gpe.GpeError) as e:
