@@ -38,11 +38,12 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rk4_shell1024_c64_traffic.json")
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the timed RK4 stage kernels (their
+    launch code, device code and shared internals)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_05447_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("gpe_internal.cuh", "stencil.cuh", "step.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -243,8 +244,10 @@ def _run_ours(args, torch, world, rank, local):
     barrier(world)
     gpe.load()
     wl = shell_workload()
+    t_build = time.perf_counter()
     grid = build_grid(gpe, wl, tuple(args.brick), args.sched, args.chunk)
     info = gpe.gpe_grid_get_info(grid)
+    t_build = time.perf_counter() - t_build  # the builder synchronises before returning
     n_active, n_stored = info.n_active, info.n_packed
     psi0 = initial_compact(gpe, inputs, wl, grid)
     dt = wl.stable_dt()
@@ -281,6 +284,7 @@ def _run_ours(args, torch, world, rank, local):
         gpe.gpe_grid_destroy(grid)
         if rank == 0:
             print(json.dumps({"quick": True, "workload": _workload_name, "dtype": args.dtype, "value": value,
+                              "grid_build_s": round(t_build, 4),
                               "ms_per_rk4_step": rk_ms, "achieved_gbs": achieved, "n_active": n_active,
                               "gpu_launches": gpu_launches}), flush=True)
         return
@@ -332,6 +336,7 @@ def _run_ours(args, torch, world, rank, local):
         "config": {"workload": "anisotropic thin ellipsoidal shell, 1024^3 box, semi-axes 490/441/392 cells, "
                                "g=2000, N=1, mask V<5mu0, RK4 real time, complex64 bulk + FP64 reductions",
                    "n_active": n_active, "n_packed": n_stored, "brick": f"{info.bx}x{info.by}x{info.bz}",
+                   "grid_build_s": round(t_build, 4),
                    "schedule": "staged" if args.sched == 0 else "wavefront",
                    "rk4_steps_per_bench_step": STEPS_PER_BENCH, "dt": dt,
                    "l2": "inputs larger than L2 (state %.0f MB + potential %.0f MB)" % (n_stored * 8 / 1e6, n_stored * 4 / 1e6),

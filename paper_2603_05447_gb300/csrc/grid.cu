@@ -74,72 +74,86 @@ __device__ __forceinline__ void cell_values(const VSource &src, const BoxD &bx, 
     }
 }
 
-// Lower bound of an analytic potential over the axis-aligned box
-// [xl,xh] x [yl,yh] x [zl,zh] (true for an unknown kind: no bound).  Both
-// potentials are separable in the squares of the coordinates, so the
-// extremes of each square over an interval give the exact range: the
-// harmonic potential's minimum directly, and for the ellipsoidal shell the
-// range [rmin, rmax] of the scaled radius, from which the minimum of
-// (rho - 1)^2 follows.
-__device__ __forceinline__ bool pot_may_select(const PotDesc &P, double cut, double xl, double xh, double yl,
-                                               double yh, double zl, double zh)
+// May an analytic potential fall below `cut` somewhere in the axis-aligned
+// box [xl,xh] x [yl,yh] x [zl,zh]?  (true for an unknown kind.)  Both
+// potentials are separable in the squares of the coordinates, so the extremes
+// of each square over an interval give the exact range: the harmonic
+// potential's minimum directly, and for the ellipsoidal shell the range
+// [rmin, rmax] of the scaled radius, from which the smallest |rho - 1|
+// follows.  Evaluated in FP32 with wide margins: it only has to be
+// conservative, the per-cell FP64 test decides.
+__device__ __forceinline__ bool pot_may_select(const PotDesc &P, double cut, float xl, float xh, float yl, float yh,
+                                               float zl, float zh)
 {
-    auto sqmin = [](double l, double h) { return (l <= 0.0 && h >= 0.0) ? 0.0 : fmin(l * l, h * h); };
-    auto sqmax = [](double l, double h) { return fmax(l * l, h * h); };
-    double vmin;
+    auto sqmin = [](float l, float h) { return (l <= 0.f && h >= 0.f) ? 0.f : fminf(l * l, h * h); };
+    auto sqmax = [](float l, float h) { return fmaxf(l * l, h * h); };
     if (P.kind == GPE_POT_HARMONIC) {
-        vmin = 0.5 * (P.p[0] * P.p[0] * sqmin(xl, xh) + P.p[1] * P.p[1] * sqmin(yl, yh) +
-                      P.p[2] * P.p[2] * sqmin(zl, zh));
-    } else if (P.kind == GPE_POT_ELLIPSOID_SHELL) {
-        const double ia = 1.0 / (P.p[1] * P.p[1]), ib = 1.0 / (P.p[2] * P.p[2]), ic = 1.0 / (P.p[3] * P.p[3]);
-        const double rmin = sqrt(sqmin(xl, xh) * ia + sqmin(yl, yh) * ib + sqmin(zl, zh) * ic);
-        const double rmax = sqrt(sqmax(xl, xh) * ia + sqmax(yl, yh) * ib + sqmax(zl, zh) * ic);
-        const double d = (rmin <= 1.0 && rmax >= 1.0) ? 0.0 : fmin(fabs(rmin - 1.0), fabs(rmax - 1.0));
-        vmin = 0.5 * P.p[0] * P.p[0] * d * d;
-    } else {
-        return true;
+        const float wx = (float)P.p[0], wy = (float)P.p[1], wz = (float)P.p[2];
+        const float vmin = 0.5f * (wx * wx * sqmin(xl, xh) + wy * wy * sqmin(yl, yh) + wz * wz * sqmin(zl, zh));
+        return vmin <= (float)cut * 1.0001f + 1e-30f;
     }
-    // the cell test rounds differently: keep a relative margin, so that the
-    // bound only ever lets more bricks through to the exact per-cell test
-    return vmin < cut * (1.0 + 1e-9) + 1e-300;
+    if (P.kind == GPE_POT_ELLIPSOID_SHELL) {
+        const float w = (float)P.p[0];
+        const float ia = 1.f / (float)(P.p[1] * P.p[1]), ib = 1.f / (float)(P.p[2] * P.p[2]),
+                    ic = 1.f / (float)(P.p[3] * P.p[3]);
+        const float rmin = sqrtf(sqmin(xl, xh) * ia + sqmin(yl, yh) * ib + sqmin(zl, zh) * ic);
+        const float rmax = sqrtf(sqmax(xl, xh) * ia + sqmax(yl, yh) * ib + sqmax(zl, zh) * ic);
+        const float d = (rmin <= 1.f && rmax >= 1.f) ? 0.f : fminf(fabsf(rmin - 1.f), fabsf(rmax - 1.f));
+        // V = w^2 d^2 / 2 < cut  <=>  |w| d < sqrt(2 cut)
+        return fabsf(w) * d <= sqrtf(2.f * (float)cut) * 1.0001f + 1e-4f * (1.f + rmax) * fabsf(w);
+    }
+    return true;
 }
 
-// (1) occupancy of every brick-grid position (lexicographic q).  Analytic
-// sources first test the brick's cell-centre box against a lower bound of
-// the potential; only bricks that may hold a selected cell are tested cell
-// by cell.
-__global__ void k_occupancy(VSource src, BoxD box, int BX, int BY, int BZ, int64_t nbx,
-                            int64_t nby, int64_t nbz, uint8_t *occ)
+// (1) occupancy of every brick-grid position (lexicographic q), 256 brick
+// positions a block.  Analytic sources: one thread a position tests the
+// brick's cell-centre box against the bound above; then the block tests the
+// cells of each candidate brick exactly.
+__global__ void k_occupancy(VSource src, BoxD box, int BX, int BY, int BZ, int64_t nbx, int64_t nby, int64_t nbz,
+                            uint8_t *occ)
 {
-    const int64_t q = blockIdx.x + (int64_t)gridDim.x * blockIdx.y;
-    if (q >= nbx * nby * nbz) return;
-    const int64_t qx = q % nbx, qy = (q / nbx) % nby, qz = q / (nbx * nby);
+    __shared__ int64_t cand[256];
+    __shared__ int ncand;
+    const int64_t nq = nbx * nby * nbz;
+    const int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (threadIdx.x == 0) ncand = 0;
+    __syncthreads();
+    if (q < nq) {
+        const int64_t qx = q % nbx, qy = (q / nbx) % nby, qz = q / (nbx * nby);
+        bool may = true;
+        if (src.mode != 0) {
+            const int64_t i0 = qx * BX, j0 = qy * BY, k0 = qz * BZ;
+            const int64_t i1 = min(i0 + BX, box.nx) - 1, j1 = min(j0 + BY, box.ny) - 1, k1 = min(k0 + BZ, box.nz) - 1;
+            const float xl = (float)(box.x0 + i0 * box.hx), xh = (float)(box.x0 + i1 * box.hx);
+            const float yl = (float)(box.y0 + j0 * box.hy), yh = (float)(box.y0 + j1 * box.hy);
+            const float zl = (float)(box.z0 + k0 * box.hz), zh = (float)(box.z0 + k1 * box.hz);
+            may = pot_may_select(src.p0, src.cut0, xl, xh, yl, yh, zl, zh);
+            if (src.mode == 2) may = may || pot_may_select(src.p1, src.cut1, xl, xh, yl, yh, zl, zh);
+        }
+        if (may)
+            cand[atomicAdd(&ncand, 1)] = q;
+        else
+            occ[q] = 0;
+    }
+    __syncthreads();
+    const int nc = ncand;
     const int BC = BX * BY * BZ;
-    if (src.mode != 0) {
-        const int64_t i0 = qx * BX, j0 = qy * BY, k0 = qz * BZ;
-        const int64_t i1 = min(i0 + BX, box.nx) - 1, j1 = min(j0 + BY, box.ny) - 1, k1 = min(k0 + BZ, box.nz) - 1;
-        const double xl = box.x0 + i0 * box.hx, xh = box.x0 + i1 * box.hx;
-        const double yl = box.y0 + j0 * box.hy, yh = box.y0 + j1 * box.hy;
-        const double zl = box.z0 + k0 * box.hz, zh = box.z0 + k1 * box.hz;
-        bool may = pot_may_select(src.p0, src.cut0, xl, xh, yl, yh, zl, zh);
-        if (src.mode == 2) may = may || pot_may_select(src.p1, src.cut1, xl, xh, yl, yh, zl, zh);
-        if (!may) {  // uniform across the block
-            if (threadIdx.x == 0) occ[q] = 0;
-            return;
+    for (int c = 0; c < nc; ++c) {
+        const int64_t qq = cand[c];
+        const int64_t qx = qq % nbx, qy = (qq / nbx) % nby, qz = qq / (nbx * nby);
+        int sel_any = 0;
+        for (int l = threadIdx.x; l < BC; l += blockDim.x) {
+            const int64_t i = qx * BX + l % BX, j = qy * BY + (l / BX) % BY, k = qz * BZ + l / (BX * BY);
+            if (i < box.nx && j < box.ny && k < box.nz) {
+                double v0, v1;
+                bool sel;
+                cell_values(src, box, i, j, k, v0, v1, sel);
+                sel_any |= sel;
+            }
         }
+        sel_any = __syncthreads_or(sel_any);
+        if (threadIdx.x == 0) occ[qq] = (uint8_t)(sel_any != 0);
     }
-    int sel_any = 0;
-    for (int l = threadIdx.x; l < BC; l += blockDim.x) {
-        int64_t i = qx * BX + l % BX, j = qy * BY + (l / BX) % BY, k = qz * BZ + l / (BX * BY);
-        if (i < box.nx && j < box.ny && k < box.nz) {
-            double v0, v1;
-            bool sel;
-            cell_values(src, box, i, j, k, v0, v1, sel);
-            sel_any |= sel;
-        }
-    }
-    sel_any = __syncthreads_or(sel_any);
-    if (threadIdx.x == 0) occ[q] = (uint8_t)(sel_any != 0);
 }
 
 __device__ __forceinline__ uint32_t compact3(uint64_t m)
@@ -526,9 +540,9 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
 
     BUILD_TRY(dev_alloc_t(&occ, nq));
     {
-        const int64_t gx = std::min<int64_t>(nq, 65535);
-        dim3 grid((unsigned)gx, (unsigned)((nq + gx - 1) / gx));
-        k_occupancy<<<grid, 128, 0, st>>>(src, bd, o.bx, o.by, o.bz, g->nbx, g->nby, g->nbz, occ);
+        const int64_t nblk_occ = (nq + 255) / 256;
+        if (nblk_occ > 0x7fffffffLL) BUILD_TRY(fail(GPE_ERR_ARG, "brick grid too large"));
+        k_occupancy<<<(unsigned)nblk_occ, 256, 0, st>>>(src, bd, o.bx, o.by, o.bz, g->nbx, g->nby, g->nbz, occ);
         BUILD_CUDA(cudaGetLastError());
     }
     Enum E;
