@@ -273,8 +273,11 @@ def _run_ours(args, torch, world, rank, local):
     peak, peak_kind = measured_peaks()
     achieved = B_ALG["c64"] * n_active / (rk_ms / 1e3) / 1e9
 
+    # DRAM bytes per RK4 step from the committed ncu capture: valid only for
+    # the captured kernels (source hash), workload and launch shape
     traffic = None
-    if os.path.exists(TRAFFIC_FILE):
+    if (os.path.exists(TRAFFIC_FILE) and args.sched == 0 and tuple(args.brick) == (8, 8, 4)
+            and args.workload == "shell1024"):
         t = json.load(open(TRAFFIC_FILE))
         if t.get("kernel_source_hash") == kernel_source_hash():
             traffic = t.get("bytes_per_step")
@@ -345,7 +348,9 @@ def _run_ours(args, torch, world, rank, local):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "RK4 step (k_rk4_staged, four launches per step)" if args.sched == 0
                      else "RK4 step (k_rk4_wave, one launch per step)", "peak_kind": peak_kind,
-                     "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms},
+                     "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms,
+                     "traffic_gbs": traffic / (rk_ms / 1e3) / 1e9 if traffic else None,
+                     "traffic_frac": traffic / (rk_ms / 1e3) / 1e9 / peak if traffic else None},
         "fp64": {"value": fp64_value, "unit": "cell-steps/s", "ms_per_rk4_step": rk128_ms,
                  "fp32_over_fp64": value / fp64_value,
                  "rel_l2_fp32_vs_fp64": err, "steps_compared": STEPS_PER_BENCH * (n128 + 1),
