@@ -346,8 +346,10 @@ def _run_ours(args, torch, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "RK4 step (k_rk4_staged, four launches per step)" if args.sched == 0
-                     else "RK4 step (k_rk4_wave, one launch per step)", "peak_kind": peak_kind,
+                     "kernel": {0: "RK4 step (k_rk4_staged, four launches per step)",
+                                1: "RK4 step (k_rk4_wave, one launch per step)",
+                                2: "RK4 step (k_rk4_wave, two launches of two stages per step)"}[args.sched],
+                     "peak_kind": peak_kind,
                      "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms,
                      "traffic_gbs": traffic / (rk_ms / 1e3) / 1e9 if traffic else None,
                      "traffic_frac": traffic / (rk_ms / 1e3) / 1e9 / peak if traffic else None},
@@ -547,7 +549,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8, help="batch workload: |dmu| tolerance")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident complex64 timing only (for profiling runs)")
-    ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront")
+    ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront, 2 two-stage wavefront")
     ap.add_argument("--chunk", type=int, default=0, help="bricks per wavefront task (0: default)")
     ap.add_argument("--brick", type=int, nargs=3, default=[8, 8, 4])
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64", help="state type of a --quick run")

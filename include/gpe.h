@@ -95,8 +95,12 @@ enum { GPE_ORDER_ZMAJOR = 0, GPE_ORDER_MORTON = 1 };
  * paper's scheme (Sec. II B); WAVE runs every stage of a time step in one
  * persistent launch, ordering (stage, chunk) tasks so that a stage of a chunk
  * starts once the previous stage has finished on every chunk its stencil
- * touches, which keeps the intermediate stage states in L2. */
-enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1 };
+ * touches, which keeps the intermediate stage states in L2 on grids whose
+ * skewed window fits there; WAVE2 runs an RK4 step as two such launches of
+ * two stages each (stages 0-1, then 2-3), a window of a third of WAVE's
+ * (imaginary-time steps have two stages: WAVE2 is WAVE there).  All three
+ * give bit-identical results. */
+enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2 };
 
 /* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
  * all three are 0), 8x8x4, 8x4x4.  chunk = bricks per wavefront task

@@ -473,7 +473,7 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
         return fail(GPE_ERR_ARG, "unknown mask mode %d", o.mask_mode);
     if (o.order != GPE_ORDER_MORTON && o.order != GPE_ORDER_ZMAJOR)
         return fail(GPE_ERR_ARG, "unknown brick order %d", o.order);
-    if (o.sched != GPE_SCHED_WAVE && o.sched != GPE_SCHED_STAGED)
+    if (o.sched != GPE_SCHED_WAVE && o.sched != GPE_SCHED_WAVE2 && o.sched != GPE_SCHED_STAGED)
         return fail(GPE_ERR_ARG, "unknown schedule %d", o.sched);
     if (o.chunk < 0 || o.chunk > 4096) return fail(GPE_ERR_ARG, "chunk must be in [0, 4096]");
 

@@ -200,8 +200,11 @@ __device__ __forceinline__ void publish(const Wave &w, int st, int c)
     if (threadIdx.x == 0) st_release(w.done + c, w.epoch + (uint32_t)st + 1u);
 }
 
+// RK4 stages first .. first + (tasks' stage count) - 1 of one step in one
+// persistent launch: first = 0 with the 4-stage task list (WAVE), or 0 and
+// then 2 with the 2-stage list (WAVE2).
 template <typename R, int BX, int BY, int BZ, bool BLEND>
-__global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, const Wave w)
+__global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, const Wave w, int first)
 {
     using CT = typename Cx<R>::T;
     constexpr int NW = KernelCfg<R>::NW;
@@ -213,8 +216,9 @@ __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, co
     for (;;) {
         const int task = next_task(w);
         if (task < 0) break;
-        const int st = task >> 28, c = task & 0x0fffffff;
-        wait_for(w, st, c);
+        const int ls = task >> 28, c = task & 0x0fffffff;  // stage within this launch
+        const int st = first + ls;
+        wait_for(w, ls, c);
         const int64_t b0 = (int64_t)c * w.cb;
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
         for (int64_t b = b0 + warp; b < b1; b += NW) {
@@ -226,7 +230,7 @@ __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, co
             default: rk4_brick<R, BX, BY, BZ, BLEND, true, 3>(a, G, b, nx, ws, s[3]); break;
             }
         }
-        publish(w, st, c);
+        publish(w, ls, c);
         if (st == 3) {
             // y3 and w of this chunk have no reader left in this step (y4,
             // in y2's buffer, is still read by the neighbour chunks' stage 3)
@@ -737,15 +741,18 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
     const GridView G = view(g);
     const int th = KernelCfg<R>::THREADS;
     const size_t smem = smem_bytes<R, BX, BY, BZ>();
-    if (g->sched == GPE_SCHED_WAVE) {
+    if (g->sched == GPE_SCHED_WAVE || g->sched == GPE_SCHED_WAVE2) {
         GPE_TRY(ensure_wave(st));
         auto k = blend ? k_rk4_wave<R, BX, BY, BZ, true> : k_rk4_wave<R, BX, BY, BZ, false>;
-        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), 4 * g->n_chunks);
+        const int ns = g->sched == GPE_SCHED_WAVE ? 4 : 2;  // stages per launch
+        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), ns * g->n_chunks);
         for (int64_t n = 0; n < nsteps; ++n) {
             a.t_off = (double)n * p->dt;
-            k<<<nblk, th, smem, s>>>(a, G, make_wave(st, 4));
-            GPE_LAUNCH_CHECK();
-            advance_wave(st, 4, nblk, false);
+            for (int first = 0; first < 4; first += ns) {
+                k<<<nblk, th, smem, s>>>(a, G, make_wave(st, ns), first);
+                GPE_LAUNCH_CHECK();
+                advance_wave(st, ns, nblk, false);
+            }
         }
         return GPE_OK;
     }
@@ -815,7 +822,7 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
     const GridView G = view(g);
     const int th = KernelCfg<R>::THREADS;
     const size_t smem = smem_bytes<R, BX, BY, BZ>();
-    if (g->sched == GPE_SCHED_WAVE) {
+    if (g->sched == GPE_SCHED_WAVE || g->sched == GPE_SCHED_WAVE2) {
         GPE_TRY(ensure_wave(st));
         auto k = k_itp_wave<R, BX, BY, BZ>;
         const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), 2 * g->n_chunks);

@@ -287,12 +287,13 @@ def test_rk4_c128_other_brick_shapes(brick):
 @pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64])
 @pytest.mark.parametrize("order", [gpe.GPE_ORDER_ZMAJOR, gpe.GPE_ORDER_MORTON])
 def test_rk4_wave_and_staged_schedules_are_bit_identical(dtype, order):
-    """Both schedules run the same per-cell arithmetic (no reductions), so
+    """All schedules run the same per-cell arithmetic (no reductions), so
     every bit agrees, whatever the chunk size or brick order."""
     case = ragged_shell()
     outs = []
     for sched, chunk in [(gpe.GPE_SCHED_STAGED, 0), (gpe.GPE_SCHED_WAVE, 0), (gpe.GPE_SCHED_WAVE, 1),
-                         (gpe.GPE_SCHED_WAVE, 3), (gpe.GPE_SCHED_WAVE, 64)]:
+                         (gpe.GPE_SCHED_WAVE, 3), (gpe.GPE_SCHED_WAVE, 64), (gpe.GPE_SCHED_WAVE2, 0),
+                         (gpe.GPE_SCHED_WAVE2, 1), (gpe.GPE_SCHED_WAVE2, 5)]:
         with Gpu(case, dtype=dtype, order=order, sched=sched, chunk=chunk) as G:
             gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), 5)
             outs.append(G.dense())
@@ -304,11 +305,12 @@ def test_rk4_wave_and_staged_schedules_are_bit_identical(dtype, order):
 def test_itp_wave_matches_staged(chunk):
     case = shell()
     outs = []
-    for sched in (gpe.GPE_SCHED_STAGED, gpe.GPE_SCHED_WAVE):
+    for sched in (gpe.GPE_SCHED_STAGED, gpe.GPE_SCHED_WAVE, gpe.GPE_SCHED_WAVE2):
         with Gpu(case, sched=sched, chunk=chunk) as G:
             gpe.gpe_step_imag(G.state, gpe.gpe_imag_params(case.g, case.dt, 1.0), 7)
             outs.append(G.dense())
     assert rel_l2(outs[1], outs[0]) <= 1e-14
+    assert rel_l2(outs[2], outs[0]) <= 1e-14
 
 
 @pytest.mark.parametrize("name", ["harmonic64", "ragged"])
