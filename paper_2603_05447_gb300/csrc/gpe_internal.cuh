@@ -305,6 +305,11 @@ struct gpe_grid {
     int64_t n_chunks = 0;
     int32_t *d_chunk_lohi = nullptr;  // [n_chunks*2]
     int32_t *d_tasks = nullptr;       // [2*n_chunks] for 2 stages, then [4*n_chunks] for 4
+    // warp-task schedule of the two-stage RK4 launches (GPE_SCHED_WAVE2): per
+    // chunk the sorted chunks its stencils read (CSR), and the task order
+    int32_t *d_dep_off = nullptr;     // [n_chunks + 1]
+    int32_t *d_dep_ids = nullptr;
+    int32_t *d_tasks_w = nullptr;     // [2*n_chunks]
     int sched = -1;                   // GPE_SCHED_* used by the step calls
     int n_slots = 1;
     double v_max = 0.0;

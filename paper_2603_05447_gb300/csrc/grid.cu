@@ -447,6 +447,9 @@ static void grid_free(gpe_grid *g)
     dev_free(g->d_rec7);
     dev_free(g->d_chunk_lohi);
     dev_free(g->d_tasks);
+    dev_free(g->d_dep_off);
+    dev_free(g->d_dep_ids);
+    dev_free(g->d_tasks_w);
     dev_free(g->d_org);
     dev_free(g->d_nbr);
     dev_free(g->d_mask);
@@ -489,7 +492,9 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     g->mask_mode = o.mask_mode;
     g->order = o.order;
     g->sched = o.sched;
-    g->cb = o.chunk > 0 ? o.chunk : std::max(1, 2048 / g->bc);
+    // bricks per wavefront task: about 2048 lattice cells for block tasks,
+    // about 1024 for the warp tasks of WAVE2
+    g->cb = o.chunk > 0 ? o.chunk : std::max(1, (o.sched == GPE_SCHED_WAVE2 ? 1024 : 2048) / g->bc);
     g->nbx = (box->nx + o.bx - 1) / o.bx;
     g->nby = (box->ny + o.by - 1) / o.by;
     g->nbz = (box->nz + o.bz - 1) / o.bz;

@@ -200,6 +200,89 @@ __device__ __forceinline__ void publish(const Wave &w, int st, int c)
     if (threadIdx.x == 0) st_release(w.done + c, w.epoch + (uint32_t)st + 1u);
 }
 
+// ------------------------------------------------------------ warp-task wavefront (WAVE2)
+// Each warp takes its own tasks (a stage of a chunk of cb bricks) in ticket
+// order, one ticket ahead; a second-stage task waits until the first stage
+// has finished on every chunk its stencils read (a per-chunk list), then
+// publishes its own completion stamp.  No block-wide barrier is involved.
+struct WaveW {
+    const int32_t *tasks;      // packed (stage << 28) | chunk
+    const int32_t *dep_off;    // [nchunks + 1]
+    const int32_t *dep_ids;    // chunks read by each chunk's stencils (itself included)
+    uint32_t *done;            // completion stamp per chunk
+    unsigned long long *ctr;   // [0] tickets, [2] error word
+    unsigned long long ticket_base;
+    uint32_t epoch;
+    int ntasks;
+    int cb;
+};
+
+// one ticket for the calling warp (-1 past the last task)
+__device__ __forceinline__ int grab_ticket(const WaveW &w)
+{
+    unsigned long long t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(&w.ctr[0], 1ull) - w.ticket_base;
+    t = __shfl_sync(0xffffffffu, t, 0);
+    return t < (unsigned long long)w.ntasks ? (int)t : -1;
+}
+
+// Wait (all 32 lanes) until every chunk in c's list has stamp >= target; at
+// most 64 entries.  Bounded like wait_chunks; once the error word is set,
+// no further wait is started.
+__device__ bool wait_deps(const WaveW &w, int c, uint32_t target)
+{
+    const int lane = threadIdx.x & 31;
+    const int d0 = w.dep_off[c], n = w.dep_off[c + 1] - d0;
+    const int i0 = lane < n ? w.dep_ids[d0 + lane] : -1;
+    const int i1 = lane + 32 < n ? w.dep_ids[d0 + lane + 32] : -1;
+    const volatile unsigned long long *err = &w.ctr[2];
+    if (*err != 0ull) return false;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < WAIT_ITERS; ++it) {
+        const bool ok = (i0 < 0 || ld_acquire(w.done + i0) >= target) && (i1 < 0 || ld_acquire(w.done + i1) >= target);
+        if (__all_sync(0xffffffffu, ok)) return true;
+        if (global_ns() - t0 > WAIT_NS || *err != 0ull) break;
+        __nanosleep(100);
+    }
+    if (lane == 0) atomicOr(&w.ctr[2], 1ull);
+    return false;
+}
+
+// RK4 stages first and first + 1 (first = 0 or 2) of one step, warp tasks
+template <typename R, int BX, int BY, int BZ, bool BLEND>
+__global__ void GPE_BOUNDS(R) k_rk4_pair(const RkArgs<R> a, const GridView G, const WaveW w, int first)
+{
+    auto &ws = warp_space<R, BX, BY, BZ>();
+    const int lane = threadIdx.x & 31;
+    const R s0 = stage_s<R, BLEND>(a, first), s1 = stage_s<R, BLEND>(a, first + 1);
+    int t = grab_ticket(w);
+    while (t >= 0) {
+        const int task = w.tasks[t];
+        const int tn = grab_ticket(w);  // the next ticket, in flight during this task
+        const int ls = task >> 28, c = task & 0x0fffffff, st = first + ls;
+        if (ls == 1) {
+            wait_deps(w, c, w.epoch + 1u);
+            __syncwarp();
+        }
+        const int64_t b0 = (int64_t)c * w.cb;
+        const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
+        for (int64_t b = b0; b < b1; ++b) {
+            const int64_t nx = b + 1 < b1 ? b + 1 : -1;
+            switch (st) {
+            case 0: rk4_brick<R, BX, BY, BZ, BLEND, true, 0>(a, G, b, nx, ws, s0); break;
+            case 1: rk4_brick<R, BX, BY, BZ, BLEND, true, 1>(a, G, b, nx, ws, s1); break;
+            case 2: rk4_brick<R, BX, BY, BZ, BLEND, true, 2>(a, G, b, nx, ws, s0); break;
+            default: rk4_brick<R, BX, BY, BZ, BLEND, true, 3>(a, G, b, nx, ws, s1); break;
+            }
+        }
+        // every lane's stores reach device scope before the warp publishes
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(w.done + c, w.epoch + (uint32_t)ls + 1u);
+        t = tn;
+    }
+}
+
 // RK4 stages first .. first + (tasks' stage count) - 1 of one step in one
 // persistent launch: first = 0 with the 4-stage task list (WAVE), or 0 and
 // then 2 with the 2-stage list (WAVE2).
@@ -631,6 +714,81 @@ static int ensure_wave(gpe_state *st)
     return GPE_OK;
 }
 
+// Warp-task schedule of the two-stage RK4 launches: per chunk the sorted set
+// of chunks holding its bricks' face neighbours (and itself), H(c) the running
+// maximum of those sets, tau(0, c) = c and tau(1, c) = H(c) + lag; tasks
+// sorted by (tau, stage, chunk).  A second-stage task's dependencies then
+// hold earlier tickets, so the holder of the smallest unfinished ticket never
+// waits.  lag: about half the resident warps, the number of first-stage
+// tasks in flight.
+static int build_schedule_w(gpe_grid *g, int64_t lag)
+{
+    if (g->d_tasks_w) return GPE_OK;
+    if (const char *e = getenv("GPE_WAVE_LAG")) lag = std::max<int64_t>(1, atoll(e));
+    const int64_t nb = g->nb, cb = g->cb;
+    const int64_t nch = (nb + cb - 1) / cb;
+    if (nch >= (1 << 28)) return fail(GPE_ERR_ARG, "too many chunks for the wavefront schedule");
+    std::vector<int32_t> nbr(nb * 6);
+    GPE_TRY_CUDA(cudaMemcpy(nbr.data(), g->d_nbr, nb * 6 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> off(nch + 1, 0), ids;
+    std::vector<int64_t> H(nch);
+    int64_t run = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+        std::vector<int32_t> d{(int32_t)c};
+        for (int64_t b = c * cb; b < std::min(nb, (c + 1) * cb); ++b)
+            for (int k = 0; k < 6; ++k)
+                if (nbr[b * 6 + k] >= 0) d.push_back((int32_t)(nbr[b * 6 + k] / cb));
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+        if (d.size() > 64) return fail(GPE_ERR_ARG, "chunk too large for the two-stage wavefront (at most 64 neighbour chunks)");
+        ids.insert(ids.end(), d.begin(), d.end());
+        off[c + 1] = (int32_t)ids.size();
+        run = std::max<int64_t>(run, d.back());
+        H[c] = run;
+    }
+    std::vector<std::pair<std::pair<int64_t, int>, int64_t>> v;
+    v.reserve(2 * nch);
+    for (int64_t c = 0; c < nch; ++c) {
+        v.push_back({{c, 0}, c});
+        v.push_back({{H[c] + lag, 1}, c});
+    }
+    std::sort(v.begin(), v.end());
+    std::vector<int32_t> tasks;
+    tasks.reserve(2 * nch);
+    for (auto &e : v) tasks.push_back((int32_t)((e.first.second << 28) | e.second));
+    int rc = dev_alloc_t(&g->d_dep_off, nch + 1);
+    if (rc == GPE_OK) rc = dev_alloc_t(&g->d_dep_ids, ids.size());
+    if (rc == GPE_OK) rc = dev_alloc_t(&g->d_tasks_w, tasks.size());
+    if (rc == GPE_OK &&
+        (cudaMemcpy(g->d_dep_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(g->d_dep_ids, ids.data(), ids.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(g->d_tasks_w, tasks.data(), tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = fail(GPE_ERR_CUDA, "schedule upload failed");
+    if (rc != GPE_OK) {
+        dev_free(g->d_dep_off);
+        dev_free(g->d_dep_ids);
+        dev_free(g->d_tasks_w);
+        g->d_dep_off = g->d_dep_ids = g->d_tasks_w = nullptr;
+    }
+    return rc;
+}
+
+static WaveW make_wave_w(gpe_state *st)
+{
+    const gpe_grid *g = st->grid;
+    WaveW w;
+    w.tasks = g->d_tasks_w;
+    w.dep_off = g->d_dep_off;
+    w.dep_ids = g->d_dep_ids;
+    w.done = st->d_done;
+    w.ctr = st->d_ctr;
+    w.ticket_base = st->ticket_base;
+    w.epoch = st->epoch;
+    w.ntasks = (int)(2 * g->n_chunks);
+    w.cb = g->cb;
+    return w;
+}
+
 static Wave make_wave(gpe_state *st, int stages)
 {
     const gpe_grid *g = st->grid;
@@ -741,17 +899,32 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
     const GridView G = view(g);
     const int th = KernelCfg<R>::THREADS;
     const size_t smem = smem_bytes<R, BX, BY, BZ>();
-    if (g->sched == GPE_SCHED_WAVE || g->sched == GPE_SCHED_WAVE2) {
+    if (g->sched == GPE_SCHED_WAVE) {
         GPE_TRY(ensure_wave(st));
         auto k = blend ? k_rk4_wave<R, BX, BY, BZ, true> : k_rk4_wave<R, BX, BY, BZ, false>;
-        const int ns = g->sched == GPE_SCHED_WAVE ? 4 : 2;  // stages per launch
-        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), ns * g->n_chunks);
+        const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), 4 * g->n_chunks);
         for (int64_t n = 0; n < nsteps; ++n) {
             a.t_off = (double)n * p->dt;
-            for (int first = 0; first < 4; first += ns) {
-                k<<<nblk, th, smem, s>>>(a, G, make_wave(st, ns), first);
+            k<<<nblk, th, smem, s>>>(a, G, make_wave(st, 4), 0);
+            GPE_LAUNCH_CHECK();
+            advance_wave(st, 4, nblk, false);
+        }
+        return GPE_OK;
+    }
+    if (g->sched == GPE_SCHED_WAVE2) {
+        GPE_TRY(ensure_wave(st));
+        auto k = blend ? k_rk4_pair<R, BX, BY, BZ, true> : k_rk4_pair<R, BX, BY, BZ, false>;
+        const int nblk = g->nsm * per_sm_for(k, th, smem);
+        const int nwarps = nblk * KernelCfg<R>::NW;
+        GPE_TRY(build_schedule_w(st->grid, std::max(1, nwarps / 2)));
+        for (int64_t n = 0; n < nsteps; ++n) {
+            a.t_off = (double)n * p->dt;
+            for (int first = 0; first < 4; first += 2) {
+                k<<<nblk, th, smem, s>>>(a, G, make_wave_w(st), first);
                 GPE_LAUNCH_CHECK();
-                advance_wave(st, ns, nblk, false);
+                // every warp took one ticket past the last task
+                st->ticket_base += 2ull * (unsigned long long)g->n_chunks + (unsigned long long)nwarps;
+                st->epoch += 2u;
             }
         }
         return GPE_OK;
