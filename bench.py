@@ -228,6 +228,22 @@ def time_rk4(gpe, torch, st, params, steps, warmup, n_active, g):
     return total, rk / (steps * STEPS_PER_BENCH)
 
 
+def time_itp(gpe, torch, st, ip, steps, warmup):
+    """Imaginary-time steps (two stencil passes and the norm each): ms per
+    step, after warm-up, CUDA events on the launching stream."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        gpe.gpe_step_imag(st, ip, STEPS_PER_BENCH)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        gpe.gpe_step_imag(st, ip, STEPS_PER_BENCH)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (steps * STEPS_PER_BENCH)
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -282,6 +298,15 @@ def _run_ours(args, torch, world, rank, local):
         if t.get("kernel_source_hash") == kernel_source_hash():
             traffic = t.get("bytes_per_step")
 
+    # ---- imaginary-time steps on the same grid (complex64, FP64 norm)
+    gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
+    ip = gpe.gpe_imag_params(wl.g, dt, wl.N)
+    itp_ms = time_itp(gpe, torch, st64, ip, args.steps, args.warmup)
+    itp = {"value": n_active / (itp_ms / 1e3), "unit": "cell-steps/s", "ms_per_itp_step": itp_ms,
+           "achieved_gbs": B_ALG["c64"] * n_active / (itp_ms / 1e3) / 1e9,
+           "alg_bytes_per_cell_step": B_ALG["c64"], "launches_per_step": 2}
+    gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
+
     if args.quick:
         gpe.gpe_state_destroy(st64)
         gpe.gpe_grid_destroy(grid)
@@ -289,7 +314,7 @@ def _run_ours(args, torch, world, rank, local):
             print(json.dumps({"quick": True, "workload": _workload_name, "dtype": args.dtype, "value": value,
                               "grid_build_s": round(t_build, 4),
                               "ms_per_rk4_step": rk_ms, "achieved_gbs": achieved, "n_active": n_active,
-                              "gpu_launches": gpu_launches}), flush=True)
+                              "ms_per_itp_step": itp_ms, "gpu_launches": gpu_launches}), flush=True)
         return
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
@@ -359,6 +384,7 @@ def _run_ours(args, torch, world, rank, local):
                  "norm_fp32": o64["norm"], "norm_fp64": o128["norm"]},
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": n_stored * 8,
                 "d2h_bytes_per_step": n_stored * 8 + 7 * 8},
+        "itp": itp,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }

@@ -329,6 +329,13 @@ __device__ __forceinline__ void fetch_recs(WS &ws, const GridView &G, int64_t b,
 #endif
 }
 
+// does the load transform XF provide a whole-segment form xf.seg(v, idx)?
+template <typename XF, typename CT, typename = void>
+struct HasSeg : std::false_type {};
+template <typename XF, typename CT>
+struct HasSeg<XF, CT, std::void_t<decltype(std::declval<const XF &>().seg(std::declval<CT (&)[4]>(), 0u))>>
+    : std::true_type {};
+
 // no operands to prefetch
 struct NoPre {
     struct P {};
@@ -369,8 +376,12 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
             CT v[4];
             if (ok) {
                 ld4<CG>(src + j, v);
+                if constexpr (HasSeg<XF, CT>::value) {
+                    xf.seg(v, j);
+                } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = xf(v[i], j + i);
+                    for (int i = 0; i < 4; ++i) v[i] = xf(v[i], j + i);
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) v[i] = czero<CT>();
@@ -529,15 +540,23 @@ struct DiagLoad {
     using CT = typename Cx<R>::T;
     R sc, hg;
     const R *E;
-    __device__ __forceinline__ CT operator()(CT v, uint32_t idx) const
+    __device__ __forceinline__ CT apply(CT v, R e) const
     {
         v.x *= sc;
         v.y *= sc;
-        const R e = __ldg(E + idx);
         const R f = e >= (R)0 ? e * ((R)1 - hg * (v.x * v.x + v.y * v.y)) : (R)0;
         v.x *= f;
         v.y *= f;
         return v;
+    }
+    __device__ __forceinline__ CT operator()(CT v, uint32_t idx) const { return apply(v, __ldg(E + idx)); }
+    // a whole segment (idx = its first cell): one vector load of E
+    __device__ __forceinline__ void seg(CT (&v)[4], uint32_t idx) const
+    {
+        R e[4];
+        ldr4(E + idx, e);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = apply(v[i], e[i]);
     }
 };
 

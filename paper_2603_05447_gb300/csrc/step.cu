@@ -346,6 +346,22 @@ struct ItpArgs {
     double N, dV;
 };
 
+// The propagator table E of a segment (E < 0 marks an inactive cell), loaded
+// ahead of the segment's update
+template <typename R>
+struct ELoad {
+    const R *E;
+    struct P {
+        R e[4];
+    };
+    __device__ __forceinline__ P operator()(uint32_t idx) const
+    {
+        P p;
+        ldr4(E + idx, p.e);
+        return p;
+    }
+};
+
 template <typename R, int BX, int BY, int BZ, bool CG>
 __device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b, int64_t next,
                                             WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R sc)
@@ -353,14 +369,12 @@ __device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView 
     using CT = typename Cx<R>::T;
     const R q4 = a.dt / (R)4;
     const DiagLoad<R> diag{sc, a.g * a.dt / (R)2, a.E};
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.psi, diag, a.ihx2, a.ihy2, a.ihz2,
-                                [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
-        R E[4];
-        ldr4(a.E + idx, E);
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.psi, diag, a.ihx2, a.ihy2, a.ihz2, ELoad<R>{a.E},
+                                [&](uint32_t idx, const typename ELoad<R>::P &p, const CT(&c)[4], const CT(&L)[4]) {
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const bool act = E[i] >= (R)0;  // E < 0 marks an inactive cell of a stored segment
+            const bool act = p.e[i] >= (R)0;  // E < 0 marks an inactive cell of a stored segment
             o[i].x = act ? c[i].x + q4 * L[i].x : (R)0;
             o[i].y = act ? c[i].y + q4 * L[i].y : (R)0;
         }
@@ -375,16 +389,14 @@ __device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView 
     using CT = typename Cx<R>::T;
     const R hg = a.g * a.dt / (R)2;
     const R q4 = a.dt / (R)4;
-    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2,
-                                [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
-        R E[4];
-        ldr4(a.E + idx, E);
+    brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2, ELoad<R>{a.E},
+                                [&](uint32_t idx, const typename ELoad<R>::P &p, const CT(&c)[4], const CT(&L)[4]) {
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             o[i].x = c[i].x + q4 * L[i].x;
             o[i].y = c[i].y + q4 * L[i].y;
-            const R f = E[i] >= (R)0 ? E[i] * ((R)1 - hg * (o[i].x * o[i].x + o[i].y * o[i].y)) : (R)0;
+            const R f = p.e[i] >= (R)0 ? p.e[i] * ((R)1 - hg * (o[i].x * o[i].x + o[i].y * o[i].y)) : (R)0;
             o[i].x *= f;
             o[i].y *= f;
             acc += (double)(o[i].x * o[i].x + o[i].y * o[i].y);
