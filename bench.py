@@ -228,6 +228,24 @@ def time_rk4(gpe, torch, st, params, steps, warmup, n_active, g):
     return total, rk / (steps * STEPS_PER_BENCH)
 
 
+# FP64 operations per stored cell and RK4 step of the stage kernels (static
+# V; an FMA counts 2): Laplacian 20 per stage; update 15, 21, 15, 19 for
+# stages 0-3
+FP64_FLOPS_PER_STORED_CELL_STEP = 4 * 20 + 15 + 21 + 15 + 19
+
+
+def fp64_roofline(n_stored, rk_ms, clocks):
+    """The complex128 step is bound by GB300's FP64 arithmetic: peak = 152
+    SMs x 2 FP64 FMA per clock x 2 flops x the SM clock (the nominal 1.25
+    TFLOP/s at 2070 MHz)."""
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
+    achieved = FP64_FLOPS_PER_STORED_CELL_STEP * n_stored / (rk_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_stored_cell_step": FP64_FLOPS_PER_STORED_CELL_STEP,
+            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x SM clock"}
+
+
 def time_itp(gpe, torch, st, ip, steps, warmup):
     """Imaginary-time steps (two stencil passes and the norm each): ms per
     step, after warm-up, CUDA events on the launching stream."""
@@ -379,6 +397,7 @@ def _run_ours(args, torch, world, rank, local):
                      "traffic_gbs": traffic / (rk_ms / 1e3) / 1e9 if traffic else None,
                      "traffic_frac": traffic / (rk_ms / 1e3) / 1e9 / peak if traffic else None},
         "fp64": {"value": fp64_value, "unit": "cell-steps/s", "ms_per_rk4_step": rk128_ms,
+                 "roofline": fp64_roofline(n_stored, rk128_ms, clk.summary()),
                  "fp32_over_fp64": value / fp64_value,
                  "rel_l2_fp32_vs_fp64": err, "steps_compared": STEPS_PER_BENCH * (n128 + 1),
                  "norm_fp32": o64["norm"], "norm_fp64": o128["norm"]},

@@ -614,6 +614,24 @@ __device__ __forceinline__ R stage_s(const RkArgs<R> &a, int st)
     return (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + c * a.dtd);
 }
 
+// x / 3, correctly rounded, without a division: q = RN(x * RN(1/3)) is within
+// one ulp of x/3, the residual r = x - 3q is exact with a fused multiply-add,
+// and RN(q + r * RN(1/3)) is the correctly rounded quotient (Markstein's
+// theorem on division with a fused multiply-add; Muller et al., Handbook of
+// Floating-Point Arithmetic, the section on Newton-Raphson-based division).
+__device__ __forceinline__ float div3(float x)
+{
+    constexpr float t = 1.0f / 3.0f;
+    const float q = __fmul_rn(x, t);
+    return __fmaf_rn(__fmaf_rn(-3.0f, q, x), t, q);
+}
+__device__ __forceinline__ double div3(double x)
+{
+    constexpr double t = 1.0 / 3.0;
+    const double q = __dmul_rn(x, t);
+    return __fma_rn(__fma_rn(-3.0, q, x), t, q);
+}
+
 // One RK4 stage (st = 0..3): operand loads and the per-segment update.  The
 // stage is a template argument so that each stage keeps only its own
 // prefetched operands in registers.
@@ -670,8 +688,8 @@ struct Rk4Body {
                     wv[i].y = -p.y[i].y + c[i].y + (R)2 * o[i].y;
                 }
             } else {
-                o[i].x = (p.y[i].x + c[i].x) / (R)3 + k * hi;
-                o[i].y = (p.y[i].y + c[i].y) / (R)3 - k * hr;
+                o[i].x = div3(p.y[i].x + c[i].x) + k * hi;
+                o[i].y = div3(p.y[i].y + c[i].y) - k * hr;
             }
         }
         if constexpr (st == 1) st4(a.w + idx, wv);
