@@ -61,6 +61,10 @@ def _load():
         lib.orc_rhs_real.restype = None
         lib.orc_rhs_real.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
                                      + [_c_f64p, ctypes.c_double, _c_f64p, _c_f64p])
+        lib.orc_rk_step.restype = ctypes.c_int
+        lib.orc_rk_step.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
+                                    + [_c_f64p, _c_f64p, ctypes.c_int, _c_f64p] + [ctypes.c_double] * 4
+                                    + [ctypes.c_int, _c_f64p, _c_f64p, _c_f64p, _c_f64p])
         lib.orc_rk4_step.restype = ctypes.c_int
         lib.orc_rk4_step.argtypes = ([ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3
                                      + [_c_f64p, _c_f64p, ctypes.c_int, _c_f64p]
@@ -166,6 +170,46 @@ def rk4_step(grid: Grid, V0, psi, g, t, dt, V1=None, knots=None, T=0.0) -> np.nd
     rc = _load().orc_rk4_step(grid.n, _pi64(grid.nbr), *grid.h, _p64(V0), _p64(V1), nk,
                               _p64(kn), T, float(g), float(t), float(dt),
                               y.view(np.float64).ctypes.data_as(_c_f64p))
+    assert rc == 0
+    return y
+
+
+# Butcher tableaux (A strictly lower, b, c) of the explicit integrators whose
+# memory-optimised forms App. A tabulates: Heun's third-order method (RKHE3),
+# the classic fourth-order method (RK4) and the fifth-order solution of the
+# Cash-Karp pair (RKCK).
+def _tableau(A, b):
+    from fractions import Fraction as F
+    s = len(b)
+    M = np.zeros((s, s))
+    for i, row in enumerate(A):
+        for j, v in enumerate(row):
+            M[i, j] = float(F(v))
+    bb = np.array([float(F(v)) for v in b])
+    return M, bb, M.sum(axis=1)
+
+
+TABLEAUX = {
+    "RKHE3": _tableau([[], ["1/3"], ["0", "2/3"]], ["1/4", "0", "3/4"]),
+    "RK4": _tableau([[], ["1/2"], ["0", "1/2"], ["0", "0", "1"]], ["1/6", "1/3", "1/3", "1/6"]),
+    "RKCK": _tableau([[], ["1/5"], ["3/40", "9/40"], ["3/10", "-9/10", "6/5"],
+                      ["-11/54", "5/2", "-70/27", "35/27"],
+                      ["1631/55296", "175/512", "575/13824", "44275/110592", "253/4096"]],
+                     ["37/378", "0", "250/621", "125/594", "0", "512/1771"]),
+}
+
+
+def rk_step(grid: Grid, V0, psi, g, t, dt, method="RK4", V1=None, knots=None, T=0.0) -> np.ndarray:
+    """One explicit Runge-Kutta step in Butcher form (TABLEAUX[method]) of
+    Eq. (8); returns the new psi."""
+    A, b, c = TABLEAUX[method]
+    V0 = np.ascontiguousarray(V0, dtype=np.float64)
+    V1, nk, kn, T = _ramp_args(V1, knots, T)
+    y = np.array(psi, dtype=np.complex128, copy=True)
+    A = np.ascontiguousarray(A)
+    rc = _load().orc_rk_step(grid.n, _pi64(grid.nbr), *grid.h, _p64(V0), _p64(V1), nk, _p64(kn), T,
+                             float(g), float(t), float(dt), len(b), _p64(A), _p64(np.ascontiguousarray(b)),
+                             _p64(np.ascontiguousarray(c)), y.view(np.float64).ctypes.data_as(_c_f64p))
     assert rc == 0
     return y
 

@@ -202,6 +202,45 @@ int orc_rk4_step(int64_t n, const int64_t *nbr, double hx, double hy,
 }
 
 /* ------------------------------------------------------------------ */
+/* General explicit Runge-Kutta step in Butcher form (the integrators   */
+/* whose memory-optimised forms App. A tabulates: RKHE3, RK4, RKCK):    */
+/*   k_i = f(t + c_i dt, y0 + dt sum_{j<i} A_ij k_j),  i = 1..s,        */
+/*   y1  = y0 + dt sum_i b_i k_i.                                       */
+/* A is s x s, row-major, only its strictly lower part is read.         */
+/* ------------------------------------------------------------------ */
+int orc_rk_step(int64_t n, const int64_t *nbr, double hx, double hy,
+                double hz, const double *V0, const double *V1, int n_knots,
+                const double *knots, double T, double g, double t, double dt,
+                int s, const double *A, const double *b, const double *c,
+                cplx *y)
+{
+    if (s < 1 || s > 16) return -2;
+    cplx *k = malloc(sizeof(cplx) * (size_t)n * (size_t)s);
+    cplx *ys = malloc(sizeof(cplx) * (size_t)n);
+    double *Vt = malloc(sizeof(double) * (size_t)n);
+    if (!k || !ys || !Vt) {
+        free(k); free(ys); free(Vt);
+        return -1;
+    }
+    for (int i = 0; i < s; ++i) {
+        for (int64_t q = 0; q < n; ++q) {
+            cplx acc = 0.0;
+            for (int j = 0; j < i; ++j) acc += A[i * s + j] * k[(size_t)j * n + q];
+            ys[q] = y[q] + dt * acc;
+        }
+        potential_at(n, V0, V1, n_knots, knots, T, t + c[i] * dt, Vt);
+        orc_rhs_real(n, nbr, hx, hy, hz, Vt, g, ys, k + (size_t)i * n);
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        cplx acc = 0.0;
+        for (int i = 0; i < s; ++i) acc += b[i] * k[(size_t)i * n + q];
+        y[q] += dt * acc;
+    }
+    free(k); free(ys); free(Vt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Imaginary-time step (Sec. II A, Eq. (6), Eq. (7) and the text after  */
 /* it), in the paper's order:                                           */
 /*   1. diagonal half step  psi <- psi * exp(-V dt/2) * (1 - g|psi|^2 dt/2) */

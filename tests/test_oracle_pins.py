@@ -450,3 +450,114 @@ def test_adjoint_step_transpose_identity(oracle_mod):
     lhs = np.sum(np.real(np.conj(lam) * Jv))
     rhs = np.sum(np.real(np.conj(JTlam) * v))
     assert abs(lhs - rhs) / abs(lhs) < 1e-8
+
+
+# ----------------------------------------------------------------- RKHE3 / RKCK (general Butcher step)
+ORDER = {"RKHE3": 3, "RK4": 4, "RKCK": 5}
+
+
+@pytest.mark.parametrize("method", ["RKHE3", "RK4", "RKCK"])
+def test_tableaux_satisfy_the_linear_order_conditions(oracle_mod, method):
+    """b^T A^(k-1) 1 = 1/k! for k <= order (the stability polynomial agrees
+    with exp(z) to that order): a transcription error in A or b fails here."""
+    A, b, c = oracle_mod.TABLEAUX[method]
+    assert np.allclose(c, A.sum(axis=1), atol=0)
+    v = np.ones(len(b))
+    for k in range(1, ORDER[method] + 1):
+        assert abs(b @ v - 1 / math.factorial(k)) < 1e-15, (method, k)
+        v = A @ v
+
+
+@pytest.mark.parametrize("method", ["RKHE3", "RKCK"])
+def test_rk_step_g0_is_stability_function_of_propagator(oracle_mod, method):
+    """Static V, g = 0: one step is R(-i H dt) psi with the stability function
+    R(z) = 1 + z b^T (I - z A)^-1 1, formed here as a dense matrix."""
+    A, b, _ = oracle_mod.TABLEAUX[method]
+    box = inputs.Box(7, 6, 6, 0.3, 0.35, 0.4)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.7, 41), (0.3, 0.35, 0.4))
+    V = np.random.default_rng(42).uniform(0, 4, g.n)
+    psi = cvec(g.n, 43)
+    dt = 0.004
+    Z = -1j * dt * dense_H(g, V)
+    # R(Z) = I + sum_k (b^T A^(k-1) 1) Z^k  (A is nilpotent: finitely many terms)
+    R = np.eye(g.n, dtype=complex)
+    v, Zk = np.ones(len(b)), np.eye(g.n, dtype=complex)
+    for _ in range(len(b)):
+        Zk = Zk @ Z
+        R = R + (b @ v) * Zk
+        v = A @ v
+    out = oracle_mod.rk_step(g, V, psi, 0.0, 0.0, dt, method)
+    assert relerr(out, R @ psi) < 1e-13
+
+
+def test_rk_step_with_rk4_tableau_equals_classic_rk4(oracle_mod):
+    box = inputs.Box(6, 5, 7, 0.3, 0.3, 0.3)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 44), 0.3)
+    rng = np.random.default_rng(45)
+    V0, V1 = rng.uniform(0, 3, g.n), rng.uniform(0, 3, g.n)
+    psi = cvec(g.n, 46) * 0.3
+    knots = np.array([0.1, 0.7, 0.2, 0.9])
+    a = oracle_mod.rk_step(g, V0, psi, 3.0, 0.05, 0.004, "RK4", V1, knots, 0.3)
+    b = oracle_mod.rk4_step(g, V0, psi, 3.0, 0.05, 0.004, V1, knots, 0.3)
+    assert relerr(a, b) < 1e-14
+
+
+@pytest.mark.parametrize("method", ["RKHE3", "RKCK"])
+def test_rk_order_against_matrix_exponential_with_time_dependent_shift(oracle_mod, method):
+    """As for RK4: a ramped uniform shift commutes with H, so the exact
+    solution is known; halving dt must cut the error by about 2^order, which
+    also pins the stage times c."""
+    box = inputs.Box(6, 6, 5, 0.35, 0.35, 0.35)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 47), 0.35)
+    V0 = np.random.default_rng(48).uniform(0, 2, g.n)
+    V1 = V0 + 1.0
+    knots = np.array([0.0, 3.0, -2.0, 1.0, 4.0])
+    T = 0.2
+    psi0 = cvec(g.n, 49)
+    H0 = dense_H(g, V0)
+    tt = np.linspace(0.0, T, 200001)
+    s = np.array([oracle_mod.ramp_s(knots, T, t) for t in tt[::100]])
+    S = np.trapezoid(np.interp(tt, tt[::100], s), tt)
+    exact = sla.expm(-1j * H0 * T) @ psi0 * np.exp(-1j * S)
+    errs = []
+    n0 = 40 if method == "RKHE3" else 16
+    for nsteps in (n0, 2 * n0):
+        dt = T / nsteps
+        y = psi0
+        for q in range(nsteps):
+            y = oracle_mod.rk_step(g, V0, y, 0.0, q * dt, dt, method, V1, knots, T)
+        errs.append(relerr(y, exact))
+    p = ORDER[method]
+    assert 0.6 * 2 ** p < errs[0] / errs[1] < 1.6 * 2 ** p, errs
+
+
+@pytest.mark.parametrize("method", ["RKHE3", "RKCK"])
+def test_appendix_A_memory_optimized_recurrence_equals_butcher_step(oracle_mod, method):
+    """App. A's printed a*, b* (tests/golden/memopt_rk_appA.json) with the
+    tableau's sub-diagonal: y^(1) = y0, y^(i+1) = sum_j a*_ij y^(j) + dt
+    a_{i+1,i} f(t + c_i dt, y^(i)), y1 = sum_j b*_j y^(j) + dt b_s f(t + c_s dt,
+    y^(s)), reproduce the Butcher step at g > 0 with a ramped potential."""
+    gold = json.load(open(os.path.join(GOLDEN, "memopt_rk_appA.json")))[method]
+    a_star = [[float(Fraction(v)) for v in row] for row in gold["a_star"]]
+    b_star = [float(Fraction(v)) for v in gold["b_star"]]
+    A, b, c = oracle_mod.TABLEAUX[method]
+    box = inputs.Box(6, 5, 6, 0.3, 0.3, 0.3)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 50), 0.3)
+    rng = np.random.default_rng(51)
+    V0, V1 = rng.uniform(0, 3, g.n), rng.uniform(0, 3, g.n)
+    knots = np.array([0.2, 0.6, 0.1, 0.8, 0.5])
+    T, t, dt, gg = 0.3, 0.07, 0.003, 3.0
+    y0 = cvec(g.n, 52) * 0.3
+
+    def f(tt, y):
+        s = oracle_mod.ramp_s(knots, T, tt)
+        return oracle_mod.rhs_real(g, (1 - s) * V0 + s * V1, gg, y)
+
+    n = len(b)
+    Y = [y0]
+    for i in range(1, n):          # y^(i+1) from y^(1..i)
+        nxt = sum(a_star[i - 1][j] * Y[j] for j in range(i)) + dt * A[i, i - 1] * f(t + c[i - 1] * dt, Y[i - 1])
+        Y.append(nxt)
+    y1 = sum(b_star[j] * Y[j] for j in range(n)) + dt * b[n - 1] * f(t + c[n - 1] * dt, Y[n - 1])
+    ref = oracle_mod.rk_step(g, V0, y0, gg, t, dt, method, V1, knots, T)
+    assert relerr(y1, ref) < 1e-13
