@@ -270,14 +270,23 @@ int gpe_step_imag(gpe_state *st, const gpe_imag_params *p, int64_t nsteps,
  * (1 - s(t)) V0 + s(t) V1 (GPE_V_BLEND) with s piecewise linear through
  * n_knots (2..16) values at uniform times on [0, T_ramp], constant outside.
  * t0 is the time at the start of the first step.  Asynchronous.
- * GPE_ERR_UNSTABLE if dt (sum_e 2/h_e^2 + v_max) > 2 sqrt(2) (RK4's
- * imaginary-axis stability limit for the linear part). */
-enum { GPE_RK4 = 0 };
+ * GPE_ERR_UNSTABLE if dt (sum_e 2/h_e^2 + v_max) exceeds the integrator's
+ * imaginary-axis limit for the linear part (below). */
+/* Integrators: the classic RK4 (default), Heun's third-order method RKHE3 and
+ * the fifth-order solution of the Cash-Karp pair RKCK, the three schemes whose
+ * memory-optimised stage forms App. A tabulates (Eqs. (A6)-(A7)):
+ *   y^(i+1) = sum_j a*_ij y^(j) + dt a_{i+1,i} f(t + c_i dt, y^(i)),
+ *   y1 = sum_j b*_j y^(j) + dt b_s f(t + c_s dt, y^(s)).
+ * Imaginary-axis limits of dt lambda_max: RK4 2 sqrt(2), RKHE3 sqrt(3).  The
+ * RKCK stability function exceeds 1 on the whole imaginary axis (~1 + 1.39e-4
+ * y^6); its steps are accepted up to y = 0.43, a growth of at most 1e-6 per
+ * step. */
+enum { GPE_RK4 = 0, GPE_RKHE3 = 1, GPE_RKCK = 2 };
 enum { GPE_V_STATIC = 0, GPE_V_BLEND = 1 };
 #define GPE_MAX_KNOTS 16
 typedef struct gpe_real_params {
     double g, dt;
-    int32_t integrator; /* GPE_RK4 */
+    int32_t integrator; /* GPE_RK4, GPE_RKHE3, GPE_RKCK */
     int32_t potential;  /* GPE_V_* */
     int32_t n_knots, reserved;
     double T_ramp;

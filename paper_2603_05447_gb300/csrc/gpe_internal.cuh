@@ -322,7 +322,7 @@ struct gpe_state {
     int dtype = GPE_C128;
     size_t elem = 16;       // bytes per complex element
     void *d_psi = nullptr;  // n_packed complex
-    void *d_work[3] = {nullptr, nullptr, nullptr};  // RK4 y2,y3,y4 / ITP tmp
+    void *d_work[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // RK stage states / ITP tmp
     void *d_E = nullptr;    // ITP exp(-V dt/2), state precision
     double E_dt = -1.0;     // dt that d_E was made for
     double *d_clock = nullptr;  // device time base for ramps

@@ -980,6 +980,177 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
     return record(s, left);
 }
 
+// ------------------------------------------------------------ general explicit RK (RKHE3, RKCK)
+// Memory-optimised form of App. A, Eqs. (A6)-(A7): with y^(1) = y0,
+//   y^(i+1) = sum_{j<=i} a*_ij y^(j) + dt a_{i+1,i} f(t + c_i dt, y^(i)),
+//   y1      = sum_{j<=s} b*_j  y^(j) + dt b_s     f(t + c_s dt, y^(s)).
+// Stage i reads y^(i) with its halo and the own cells of the earlier states
+// whose coefficient is not zero.
+struct RkTable {
+    int s;                 // stages
+    double c[6];           // stage times
+    double sub[6];         // a_{i+1,i} (i < s), then b_s
+    double a_star[5][5];   // rows for y^(2) .. y^(s) (App. A printed tables)
+    double b_star[6];
+    double ylim;           // dt * lambda_max accepted by gpe_step_real
+};
+
+// Heun's third-order method (RKHE3): App. A, a* = [[1],[1, 0]],
+// b* = (1/4, 3/4, 0); a_21 = 1/3, a_32 = 2/3, b_3 = 3/4; c = (0, 1/3, 2/3).
+// |R(iy)| <= 1 up to y = sqrt(3).
+static const RkTable RK_HE3 = {3,
+                               {0.0, 1.0 / 3.0, 2.0 / 3.0},
+                               {1.0 / 3.0, 2.0 / 3.0, 3.0 / 4.0},
+                               {{1.0}, {1.0, 0.0}},
+                               {1.0 / 4.0, 3.0 / 4.0, 0.0},
+                               1.7320508075688772};
+// Cash-Karp, fifth-order solution (RKCK): App. A's a* rows and b*; the
+// tableau's sub-diagonal a_21 = 1/5, a_32 = 9/40, a_43 = 6/5, a_54 = 35/27,
+// a_65 = 253/4096, b_6 = 512/1771; c = (0, 1/5, 3/10, 3/5, 1, 7/8).  Its
+// stability function exceeds 1 on the whole imaginary axis, |R(iy)| ~ 1 +
+// 1.39e-4 y^6; steps are accepted while that growth stays below 1e-6 per
+// step (y <= 0.43).
+static const RkTable RK_CK = {6,
+                              {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0},
+                              {1.0 / 5.0, 9.0 / 40.0, 6.0 / 5.0, 35.0 / 27.0, 253.0 / 4096.0, 512.0 / 1771.0},
+                              {{1.0},
+                               {5.0 / 8.0, 3.0 / 8.0},
+                               {2.0, 3.0, -4.0},
+                               {-49.0 / 81.0, 35.0 / 27.0, 200.0 / 81.0, -175.0 / 81.0},
+                               {253.0 / 12288.0, -3795.0 / 4096.0, 1375.0 / 1536.0, 2875.0 / 4096.0, 1265.0 / 4096.0}},
+                              {-991.0 / 15939.0, -3865.0 / 5313.0, 5000.0 / 5313.0, 3125.0 / 4554.0, 25.0 / 154.0, 0.0},
+                              0.43};
+
+static const RkTable *rk_table(int integrator)
+{
+    return integrator == GPE_RKHE3 ? &RK_HE3 : integrator == GPE_RKCK ? &RK_CK : nullptr;
+}
+double rk_stability_limit(int integrator)
+{
+    const RkTable *t = rk_table(integrator);
+    return t ? t->ylim : 2.0 * std::sqrt(2.0);
+}
+
+template <typename R>
+struct RkGenArgs {
+    using CT = typename Cx<R>::T;
+    CT *y[6];        // y^(1) = psi, y^(2..6) = work buffers
+    const R *V0;
+    const R *V1;
+    R ihx2, ihy2, ihz2, g;
+    Ramp ramp;
+    double t_off;    // step start relative to *ramp.clock
+    double tc;       // c_i dt
+    int tile, out;   // y^(i) and the state written (y^(i+1), or y^(1) for y1)
+    int nsrc;        // own-cell terms
+    int src[5];
+    R coef[5];
+    R ctile;         // coefficient of y^(i) itself
+    R kdt;           // dt a_{i+1,i} (dt b_s in the last stage)
+};
+
+template <typename R, int BX, int BY, int BZ, bool BLEND>
+__global__ void GPE_BOUNDS(R) k_rk_stage(const RkGenArgs<R> a, const GridView G)
+{
+    using CT = typename Cx<R>::T;
+    constexpr int NW = KernelCfg<R>::NW;
+    auto &ws = warp_space<R, BX, BY, BZ>();
+    const int warp = threadIdx.x >> 5;
+    const R s = BLEND ? (R)ramp_s(a.ramp, *a.ramp.clock + a.t_off + a.tc) : (R)0;
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
+        brick_apply<BX, BY, BZ, false>(ws, G, b, b + stride < G.nb ? b + stride : -1, a.y[a.tile], Identity(), a.ihx2,
+                                       a.ihy2, a.ihz2, [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
+            R V0[4], V1[4];
+            ldr4(a.V0 + idx, V0);
+            if (BLEND) ldr4(a.V1 + idx, V1);
+            CT acc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[i].x = a.ctile * c[i].x;
+                acc[i].y = a.ctile * c[i].y;
+            }
+            for (int j = 0; j < a.nsrc; ++j) {
+                CT yj[4];
+                ld4<false>(a.y[a.src[j]] + idx, yj);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[i].x += a.coef[j] * yj[i].x;
+                    acc[i].y += a.coef[j] * yj[i].y;
+                }
+            }
+            CT o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!(V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
+                    o[i] = czero<CT>();
+                    continue;
+                }
+                const R V = BLEND ? ((R)1 - s) * V0[i] + s * V1[i] : V0[i];
+                const R w = V + a.g * (c[i].x * c[i].x + c[i].y * c[i].y);
+                const R hr = (R)(-0.5) * L[i].x + w * c[i].x;
+                const R hi = (R)(-0.5) * L[i].y + w * c[i].y;
+                // f = -i (hr + i hi) = hi - i hr
+                o[i].x = acc[i].x + a.kdt * hi;
+                o[i].y = acc[i].y - a.kdt * hr;
+            }
+            st4(a.y[a.out] + idx, o);
+        });
+    }
+}
+
+template <typename R, int BX, int BY, int BZ>
+static int rkgen_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, double t0, cudaStream_t s)
+{
+    using CT = typename Cx<R>::T;
+    const gpe_grid *g = st->grid;
+    const RkTable &T = *rk_table(p->integrator);
+    const bool blend = p->potential == GPE_V_BLEND;
+    RkGenArgs<R> a{};
+    a.y[0] = (CT *)st->d_psi;
+    for (int i = 1; i < 6; ++i) a.y[i] = (CT *)st->d_work[i - 1];
+    a.V0 = (const R *)potential_ptr(st, 0);
+    a.V1 = blend ? (const R *)potential_ptr(st, 1) : nullptr;
+    if (!a.V0 || (blend && !a.V1)) return fail(GPE_ERR_STATE, "potential slot missing");
+    a.ihx2 = (R)(1.0 / (g->box.hx * g->box.hx));
+    a.ihy2 = (R)(1.0 / (g->box.hy * g->box.hy));
+    a.ihz2 = (R)(1.0 / (g->box.hz * g->box.hz));
+    a.g = (R)p->g;
+    a.ramp.clock = st->d_clock;
+    a.ramp.T = p->T_ramp;
+    a.ramp.n_knots = p->n_knots;
+    for (int k = 0; k < GPE_MAX_KNOTS; ++k) a.ramp.knots[k] = p->knots[k];
+    if (blend) {
+        k_set_scalar<<<1, 1, 0, s>>>(st->d_clock, t0);
+        GPE_LAUNCH_CHECK();
+    }
+    auto k = blend ? k_rk_stage<R, BX, BY, BZ, true> : k_rk_stage<R, BX, BY, BZ, false>;
+    const size_t smem = smem_bytes<R, BX, BY, BZ>();
+    const int nblk = blocks_for<R>(k, g, smem);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        a.t_off = (double)n * p->dt;
+        for (int i = 0; i < T.s; ++i) {  // stage i + 1 of App. A
+            const bool last = i == T.s - 1;
+            const double *row = last ? T.b_star : T.a_star[i];
+            a.tile = i;
+            a.out = last ? 0 : i + 1;
+            a.tc = T.c[i] * p->dt;
+            a.kdt = (R)(T.sub[i] * p->dt);
+            a.ctile = (R)row[i];
+            a.nsrc = 0;
+            for (int j = 0; j < i; ++j)
+                if (row[j] != 0.0) {
+                    a.src[a.nsrc] = j;
+                    a.coef[a.nsrc] = (R)row[j];
+                    ++a.nsrc;
+                }
+            k<<<nblk, KernelCfg<R>::THREADS, smem, s>>>(a, view(g));
+            GPE_LAUNCH_CHECK();
+        }
+    }
+    return GPE_OK;
+}
+
 template <typename R, int BX, int BY, int BZ>
 static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cudaStream_t s)
 {
@@ -1122,7 +1293,7 @@ extern "C" int gpe_state_destroy(gpe_state *st)
     if (!st) return GPE_OK;
     cudaDeviceSynchronize();
     dev_free(st->d_psi);
-    for (int i = 0; i < 3; ++i) dev_free(st->d_work[i]);
+    for (int i = 0; i < 6; ++i) dev_free(st->d_work[i]);
     dev_free(st->d_E);
     dev_free(st->d_clock);
     dev_free(st->d_done);
@@ -1290,7 +1461,8 @@ extern "C" int gpe_step_real(gpe_state *st, const gpe_real_params *p, int64_t ns
     GPE_TRY(check_state(st));
     if (!p) return fail(GPE_ERR_ARG, "params is NULL");
     if (nsteps < 0) return fail(GPE_ERR_ARG, "nsteps < 0");
-    if (p->integrator != GPE_RK4) return fail(GPE_ERR_ARG, "unknown integrator %d", p->integrator);
+    if (p->integrator != GPE_RK4 && p->integrator != GPE_RKHE3 && p->integrator != GPE_RKCK)
+        return fail(GPE_ERR_ARG, "unknown integrator %d", p->integrator);
     if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(GPE_ERR_ARG, "dt must be finite and > 0");
     if (!std::isfinite(p->g)) return fail(GPE_ERR_ARG, "g must be finite");
     if (p->potential == GPE_V_BLEND) {
@@ -1302,12 +1474,21 @@ extern "C" int gpe_step_real(gpe_state *st, const gpe_real_params *p, int64_t ns
     }
     const gpe_box &b = st->grid->box;
     const double lam = 2.0 / (b.hx * b.hx) + 2.0 / (b.hy * b.hy) + 2.0 / (b.hz * b.hz) + st->grid->v_max;
-    if (p->dt * lam > 2.0 * std::sqrt(2.0))
-        return fail(GPE_ERR_UNSTABLE, "dt*lambda_max = %.3g exceeds RK4's limit 2*sqrt(2)", p->dt * lam);
+    const double ylim = rk_stability_limit(p->integrator);
+    if (p->dt * lam > ylim)
+        return fail(GPE_ERR_UNSTABLE, "dt*lambda_max = %.3g exceeds the integrator's limit %.3g", p->dt * lam, ylim);
     if (nsteps == 0) return GPE_OK;
-    GPE_TRY(ensure_work(st, 3));
     cudaStream_t s = S(stream);
     const bool c128 = st->dtype == GPE_C128;
+    if (p->integrator != GPE_RK4) {
+        GPE_TRY(ensure_work(st, rk_table(p->integrator)->s - 1));
+#define RKG_CASE(id, X, Y, Z) \
+    case id: return c128 ? rkgen_run<double, X, Y, Z>(st, p, nsteps, t0, s) : rkgen_run<float, X, Y, Z>(st, p, nsteps, t0, s);
+        switch (st->grid->shape) { GPE_SHAPES(RKG_CASE) }
+#undef RKG_CASE
+        return fail(GPE_ERR_STATE, "bad brick shape");
+    }
+    GPE_TRY(ensure_work(st, 3));
 #define RK_CASE(id, X, Y, Z) \
     case id: return c128 ? rk4_run<double, X, Y, Z>(st, p, nsteps, t0, s) : rk4_run<float, X, Y, Z>(st, p, nsteps, t0, s);
     switch (st->grid->shape) { GPE_SHAPES(RK_CASE) }

@@ -40,7 +40,7 @@ GPE_F64, GPE_F32 = 1, 2
 GPE_POT_HARMONIC, GPE_POT_ELLIPSOID_SHELL = 1, 2
 GPE_C128, GPE_C64 = 1, 2
 GPE_LAYOUT_DENSE, GPE_LAYOUT_COMPACT = 0, 1
-GPE_RK4 = 0
+GPE_RK4, GPE_RKHE3, GPE_RKCK = 0, 1, 2
 GPE_V_STATIC, GPE_V_BLEND = 0, 1
 GPE_MAX_KNOTS = 16
 
@@ -291,10 +291,10 @@ def make_potential(kind, *params) -> gpe_potential:
     return p
 
 
-def real_params(g, dt, potential=GPE_V_STATIC, knots=None, T_ramp=0.0) -> gpe_real_params:
+def real_params(g, dt, potential=GPE_V_STATIC, knots=None, T_ramp=0.0, integrator=GPE_RK4) -> gpe_real_params:
     p = gpe_real_params()
     p.g, p.dt = float(g), float(dt)
-    p.integrator = GPE_RK4
+    p.integrator = integrator
     p.potential = potential
     if knots is not None:
         knots = list(knots)
