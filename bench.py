@@ -316,6 +316,25 @@ def _run_ours(args, torch, world, rank, local):
         if t.get("kernel_source_hash") == kernel_source_hash():
             traffic = t.get("bytes_per_step")
 
+    # ---- the other memory-optimised integrators of App. A on the same grid
+    integ = {}
+    if not args.quick or args.integrators:
+        for name, code, ylim in (("RKHE3", gpe.GPE_RKHE3, 3 ** 0.5), ("RKCK", gpe.GPE_RKCK, 0.43)):
+            gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
+            # the headline dt (dt lambda_max = 0.2) is inside both limits
+            p_i = gpe.real_params(wl.g, dt, integrator=code)
+            for _ in range(max(1, args.warmup)):
+                gpe.gpe_step_real(st64, p_i, STEPS_PER_BENCH // 10)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(torch.cuda.current_stream())
+            gpe.gpe_step_real(st64, p_i, STEPS_PER_BENCH)
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / STEPS_PER_BENCH
+            integ[name] = {"value": n_active / (ms / 1e3), "unit": "cell-steps/s", "ms_per_step": ms,
+                           "stages": 3 if name == "RKHE3" else 6}
+
     # ---- imaginary-time steps on the same grid (complex64, FP64 norm)
     gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
     ip = gpe.gpe_imag_params(wl.g, dt, wl.N)
@@ -332,7 +351,8 @@ def _run_ours(args, torch, world, rank, local):
             print(json.dumps({"quick": True, "workload": _workload_name, "dtype": args.dtype, "value": value,
                               "grid_build_s": round(t_build, 4),
                               "ms_per_rk4_step": rk_ms, "achieved_gbs": achieved, "n_active": n_active,
-                              "ms_per_itp_step": itp_ms, "gpu_launches": gpu_launches}), flush=True)
+                              "ms_per_itp_step": itp_ms, "integrators": integ or None,
+                              "gpu_launches": gpu_launches}), flush=True)
         return
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
@@ -404,6 +424,7 @@ def _run_ours(args, torch, world, rank, local):
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": n_stored * 8,
                 "d2h_bytes_per_step": n_stored * 8 + 7 * 8},
         "itp": itp,
+        "integrators": integ,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
@@ -592,6 +613,7 @@ def main():
                          "time the other workloads (one JSON line each)")
     ap.add_argument("--shells", type=int, default=64, help="batch workload: number of shells")
     ap.add_argument("--tol", type=float, default=1e-8, help="batch workload: |dmu| tolerance")
+    ap.add_argument("--integrators", action="store_true", help="a --quick run also times RKHE3 and RKCK")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident complex64 timing only (for profiling runs)")
     ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront, 2 two-stage wavefront")
