@@ -224,6 +224,17 @@ int gpe_state_store(const gpe_state *st, void *psi, int layout, int on_device,
 /* dst <- src (same grid and dtype).  Asynchronous. */
 int gpe_state_copy(gpe_state *dst, const gpe_state *src, gpe_stream stream);
 
+/* Remap a state onto another grid over the same box: the regrid between ramp
+ * stages of Sec. V (the region of interest is selected again and the
+ * wavefunction remapped between the old and new grids).  Every cell active
+ * in both grids takes src's value; cells active only in dst's grid become 0;
+ * src's cells outside dst's region are dropped (renormalise afterwards if
+ * the norm should be kept).  The grids must share box sizes, spacings and
+ * origin (bit-identical gpe_box); brick shapes and orders may differ.  Same
+ * dtype, distinct states, same device.  GPE_ERR_ARG otherwise.
+ * Asynchronous. */
+int gpe_state_remap(gpe_state *dst, const gpe_state *src, gpe_stream stream);
+
 /* Failure detection self-test: one warp waits (with the same bounded wait the
  * wavefront schedule uses) for a completion stamp that nothing sets; the wait
  * gives up after limit_s seconds (0 < limit_s <= 10) and reports it.  Sets

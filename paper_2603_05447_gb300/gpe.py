@@ -132,6 +132,7 @@ _SIGS = {
     "gpe_state_load": (C.c_int, [_P, _P, C.c_int, C.c_int, _P]),
     "gpe_state_store": (C.c_int, [_P, _P, C.c_int, C.c_int, _P]),
     "gpe_state_copy": (C.c_int, [_P, _P, _P]),
+    "gpe_state_remap": (C.c_int, [_P, _P, _P]),
     "gpe_state_device_ptr": (C.c_int, [_P, C.POINTER(_P)]),
     "gpe_state_destroy": (C.c_int, [_P]),
     "gpe_step_imag": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_int64, _P]),
@@ -408,6 +409,12 @@ def gpe_state_store(state, psi, layout, stream=None):
 
 def gpe_state_copy(dst, src, stream=None):
     _check(load().gpe_state_copy(dst, src, stream_handle(stream)))
+
+
+def gpe_state_remap(dst, src, stream=None):
+    """Remap src onto dst's grid (same box): cells active in both keep src's
+    value, the others of dst become 0 (Sec. V regrid between ramp stages)."""
+    _check(load().gpe_state_remap(dst, src, stream_handle(stream)))
 
 
 def gpe_state_device_ptr(state) -> int:
