@@ -202,11 +202,18 @@ int gpe_tf_mu_analytic(const gpe_box *box, const gpe_potential *pot,
                        double g, double N, double *mu, gpe_stream stream);
 
 /* ------------------------------------------------------------------ states */
-enum { GPE_C128 = 1, GPE_C64 = 2 };
+enum { GPE_C128 = 1, GPE_C64 = 2, GPE_R64 = 3, GPE_R32 = 4 };
 enum { GPE_LAYOUT_DENSE = 0, GPE_LAYOUT_COMPACT = 1 };
 
 /* A wavefunction on a grid, complex128 or complex64 (bulk precision).  The
- * state keeps a reference to the grid: destroy states before their grid. */
+ * real types GPE_R64 / GPE_R32 hold a real-valued wavefunction for
+ * imaginary-time work: the imaginary-time step keeps a real wavefunction
+ * real, so half the bytes suffice (Sec. II A).  Real states support load,
+ * store, copy, remap, gpe_step_imag, gpe_observables and gpe_ground_state;
+ * the calls that need complex values (real-time steps, overlaps, batches,
+ * ramp gradients) refuse them with GPE_ERR_ARG.  Load and store use arrays
+ * of double / float.  The state keeps a reference to the grid: destroy
+ * states before their grid. */
 int gpe_state_create(gpe_grid *grid, int dtype, gpe_state **out);
 
 /* Load psi from a dense box array (inactive cells are ignored) or from the

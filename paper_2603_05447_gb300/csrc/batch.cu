@@ -288,6 +288,7 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
     for (int i = 1; i < n; ++i)
         if (states[i]->dtype != dtype || states[i]->grid->shape != shape)
             return fail(GPE_ERR_ARG, "batch states must share dtype and brick shape (state %d differs)", i);
+    if (dtype != GPE_C128 && dtype != GPE_C64) return fail(GPE_ERR_ARG, "batches hold complex states");
     gpe_batch *B = new gpe_batch();
     B->n = n;
     B->dtype = dtype;

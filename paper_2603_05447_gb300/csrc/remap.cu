@@ -1,7 +1,7 @@
 // remap.cu -- a state carried from one grid to another over the same box:
 // the wavefunction remapped between the old and new grids when the region
 // of interest is selected again between ramp stages (Sec. V).
-#include "gpe_internal.cuh"
+#include "stencil.cuh"
 
 namespace gpe {
 
@@ -28,9 +28,7 @@ __global__ void k_remap(CT *dst, const CT *src, RemapSide D, RemapSide S, int64_
         uint32_t jd;
         if (!seg_index(D.rec[b], l >> 2, jd)) continue;
         jd += (uint32_t)(l & 3);
-        CT v;
-        v.x = 0;
-        v.y = 0;
+        CT v = czero<CT>();
         if ((D.mask[b * (dbc / 32) + (l >> 5)] >> (l & 31)) & 1u) {
             const int64_t i = D.org[3 * b] + l % D.bx;
             const int64_t j = D.org[3 * b + 1] + (l / D.bx) % D.by;
@@ -79,12 +77,24 @@ extern "C" int gpe_state_remap(gpe_state *dst, const gpe_state *src, gpe_stream 
     const int64_t n_lattice = dg->nb * (int64_t)dg->bc;
     const int blocks = (int)std::min<int64_t>((n_lattice + 255) / 256, (int64_t)dg->nsm * 16);
     if (n_lattice == 0) return GPE_OK;
-    if (dst->dtype == GPE_C128)
+    switch (dst->dtype) {
+    case GPE_C128:
         k_remap<double2><<<blocks, 256, 0, s>>>((double2 *)dst->d_psi, (const double2 *)src->d_psi, side(dg), side(sg),
                                                 n_lattice);
-    else
+        break;
+    case GPE_C64:
         k_remap<float2><<<blocks, 256, 0, s>>>((float2 *)dst->d_psi, (const float2 *)src->d_psi, side(dg), side(sg),
                                                n_lattice);
+        break;
+    case GPE_R64:
+        k_remap<double><<<blocks, 256, 0, s>>>((double *)dst->d_psi, (const double *)src->d_psi, side(dg), side(sg),
+                                               n_lattice);
+        break;
+    default:
+        k_remap<float><<<blocks, 256, 0, s>>>((float *)dst->d_psi, (const float *)src->d_psi, side(dg), side(sg),
+                                              n_lattice);
+        break;
+    }
     GPE_LAUNCH_CHECK();
     return GPE_OK;
 }

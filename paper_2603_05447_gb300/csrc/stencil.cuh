@@ -65,13 +65,108 @@ struct Seg {
     static_assert(32 % PLANE == 0 && NSEG % 32 == 0, "brick shape must tile the warp");
 };
 
+// Values are complex (float2, double2) or, for real-valued imaginary-time
+// states, real (float, double); these helpers serve both.
+template <typename CT>
+__host__ __device__ constexpr bool is_cplx()
+{
+    return !std::is_arithmetic<CT>::value;
+}
+template <typename CT>
+struct RealOf {
+    using T = CT;
+};
+template <>
+struct RealOf<float2> {
+    using T = float;
+};
+template <>
+struct RealOf<double2> {
+    using T = double;
+};
+
 template <typename CT>
 __device__ __forceinline__ CT czero()
 {
-    CT z;
-    z.x = 0;
-    z.y = 0;
-    return z;
+    if constexpr (is_cplx<CT>()) {
+        CT z;
+        z.x = 0;
+        z.y = 0;
+        return z;
+    } else {
+        return CT(0);
+    }
+}
+// |v|^2
+template <typename CT>
+__device__ __forceinline__ typename RealOf<CT>::T norm2(const CT &v)
+{
+    if constexpr (is_cplx<CT>())
+        return v.x * v.x + v.y * v.y;
+    else
+        return v * v;
+}
+// v * f, f real
+template <typename CT, typename R>
+__device__ __forceinline__ CT scale(CT v, R f)
+{
+    if constexpr (is_cplx<CT>()) {
+        v.x *= f;
+        v.y *= f;
+        return v;
+    } else {
+        return v * f;
+    }
+}
+// c + a L, a real
+template <typename CT, typename R>
+__device__ __forceinline__ CT axpy(const CT &c, R a, const CT &L)
+{
+    if constexpr (is_cplx<CT>()) {
+        CT o;
+        o.x = c.x + a * L.x;
+        o.y = c.y + a * L.y;
+        return o;
+    } else {
+        return c + a * L;
+    }
+}
+// Re(conj(a) b)
+template <typename CT>
+__device__ __forceinline__ typename RealOf<CT>::T dotre(const CT &a, const CT &b)
+{
+    if constexpr (is_cplx<CT>())
+        return a.x * b.x + a.y * b.y;
+    else
+        return a * b;
+}
+template <typename CT>
+__device__ __forceinline__ bool finite_v(const CT &v)
+{
+    if constexpr (is_cplx<CT>())
+        return isfinite(v.x) && isfinite(v.y);
+    else
+        return isfinite(v);
+}
+// one component of the 7-point Laplacian (Eq. (B1)) from opposite-neighbour
+// sums: (x- + x+)/hx^2 + (y- + y+)/hy^2 + (z- + z+)/hz^2 - c6 c
+template <typename R>
+__device__ __forceinline__ R lap1(R xp, R xm, R yp, R ym, R zp, R zm, R c, R ihx2, R ihy2, R ihz2, R c6)
+{
+    return (xp + xm) * ihx2 + (yp + ym) * ihy2 + (zp + zm) * ihz2 - c6 * c;
+}
+template <typename CT, typename R>
+__device__ __forceinline__ CT lapv(const CT &xp, const CT &xm, const CT &yp, const CT &ym, const CT &zp, const CT &zm,
+                                   const CT &c, R ihx2, R ihy2, R ihz2, R c6)
+{
+    if constexpr (is_cplx<CT>()) {
+        CT L;
+        L.x = lap1(xp.x, xm.x, yp.x, ym.x, zp.x, zm.x, c.x, ihx2, ihy2, ihz2, c6);
+        L.y = lap1(xp.y, xm.y, yp.y, ym.y, zp.y, zm.y, c.y, ihx2, ihy2, ihz2, c6);
+        return L;
+    } else {
+        return lap1(xp, xm, yp, ym, zp, zm, c, ihx2, ihy2, ihz2, c6);
+    }
 }
 
 __device__ __forceinline__ float2 shfl_up(float2 v, int d)
@@ -158,6 +253,33 @@ __device__ __forceinline__ void st4(double2 *p, const double2 (&v)[4])
                      "d"(v[2 * h + 1].x), "d"(v[2 * h + 1].y)
                      : "memory");
 }
+// 4 consecutive reals of a real-valued state (one segment, 16- or 32-byte
+// aligned); CG as for ld4 above
+template <bool CG>
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
+{
+    if (CG)
+        asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+    else
+        asm volatile("ld.global.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+}
+template <bool CG>
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
+{
+    if (CG)
+        asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+    else
+        asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4])
+{
+    asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]) : "memory");
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4])
+{
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3]) : "memory");
+}
+
 // 4 consecutive reals (16- or 32-byte aligned), read-only data
 __device__ __forceinline__ void ldr4(const float *p, float (&v)[4])
 {
@@ -250,10 +372,10 @@ struct WarpSpace {
     }
 };
 
-template <typename R, int BX, int BY, int BZ>
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
 constexpr size_t smem_bytes()
 {
-    return (size_t)KernelCfg<R>::NW * sizeof(WarpSpace<typename Cx<R>::T, BX, BY, BZ>);
+    return (size_t)KernelCfg<R>::NW * sizeof(WarpSpace<CT, BX, BY, BZ>);
 }
 
 // the calling warp's workspace (call once per kernel: it resets the
@@ -266,11 +388,11 @@ constexpr int min_blocks()
     return fit < 1 ? 1 : (fit < cap ? fit : cap);
 }
 
-template <typename R, int BX, int BY, int BZ>
-__device__ __forceinline__ WarpSpace<typename Cx<R>::T, BX, BY, BZ> &warp_space()
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
+__device__ __forceinline__ WarpSpace<CT, BX, BY, BZ> &warp_space()
 {
     extern __shared__ __align__(16) unsigned char gpe_smem[];
-    auto &ws = reinterpret_cast<WarpSpace<typename Cx<R>::T, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
+    auto &ws = reinterpret_cast<WarpSpace<CT, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
 #if GPE_REC_AHEAD
     if ((threadIdx.x & 31) == 0) ws.nrec_b = -1;
     __syncwarp();
@@ -473,8 +595,7 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
         for (int i = 0; i < 4; ++i) {
             const CT l = i == 0 ? xm : c[i - 1];
             const CT rr = i == 3 ? xp : c[i + 1];
-            L[i].x = (rr.x + l.x) * ihx2 + (yp[i].x + ym[i].x) * ihy2 + (zp[i].x + zm[i].x) * ihz2 - c6 * c[i].x;
-            L[i].y = (rr.y + l.y) * ihx2 + (yp[i].y + ym[i].y) * ihy2 + (zp[i].y + zm[i].y) * ihz2 - c6 * c[i].y;
+            L[i] = lapv(rr, l, yp[i], ym[i], zp[i], zm[i], c[i], ihx2, ihy2, ihz2, c6);
         }
         body(R0.off + 4u * (uint32_t)r, pre, c, L);
     };
@@ -535,19 +656,15 @@ __device__ __forceinline__ double ramp_s(const Ramp &r, double t)
     return (1.0 - w) * r.knots[k] + w * r.knots[k + 1];
 }
 
-template <typename R>
+template <typename R, typename CT = typename Cx<R>::T>
 struct DiagLoad {
-    using CT = typename Cx<R>::T;
     R sc, hg;
     const R *E;
     __device__ __forceinline__ CT apply(CT v, R e) const
     {
-        v.x *= sc;
-        v.y *= sc;
-        const R f = e >= (R)0 ? e * ((R)1 - hg * (v.x * v.x + v.y * v.y)) : (R)0;
-        v.x *= f;
-        v.y *= f;
-        return v;
+        v = scale(v, sc);
+        const R f = e >= (R)0 ? e * ((R)1 - hg * norm2(v)) : (R)0;
+        return scale(v, f);
     }
     __device__ __forceinline__ CT operator()(CT v, uint32_t idx) const { return apply(v, __ldg(E + idx)); }
     // a whole segment (idx = its first cell): one vector load of E

@@ -335,9 +335,8 @@ __global__ void GPE_BOUNDS(R) k_rk4_wave(const RkArgs<R> a, const GridView G, co
 // sqrt(N / (sum |psi|^2 dV)) is stored for the next step's stage A (or the
 // end of the call).  E = 0 on inactive cells of stored segments (V = +inf),
 // so those stay zero.
-template <typename R>
+template <typename R, typename CT = typename Cx<R>::T>
 struct ItpArgs {
-    using CT = typename Cx<R>::T;
     CT *psi;
     CT *tmp;
     const R *E;
@@ -362,31 +361,28 @@ struct ELoad {
     }
 };
 
-template <typename R, int BX, int BY, int BZ, bool CG>
-__device__ __forceinline__ void itp_brick_a(const ItpArgs<R> &a, const GridView &G, int64_t b, int64_t next,
-                                            WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R sc)
+template <typename R, typename CT, int BX, int BY, int BZ, bool CG>
+__device__ __forceinline__ void itp_brick_a(const ItpArgs<R, CT> &a, const GridView &G, int64_t b, int64_t next,
+                                            WarpSpace<CT, BX, BY, BZ> &ws, R sc)
 {
-    using CT = typename Cx<R>::T;
     const R q4 = a.dt / (R)4;
-    const DiagLoad<R> diag{sc, a.g * a.dt / (R)2, a.E};
+    const DiagLoad<R, CT> diag{sc, a.g * a.dt / (R)2, a.E};
     brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.psi, diag, a.ihx2, a.ihy2, a.ihz2, ELoad<R>{a.E},
                                 [&](uint32_t idx, const typename ELoad<R>::P &p, const CT(&c)[4], const CT(&L)[4]) {
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool act = p.e[i] >= (R)0;  // E < 0 marks an inactive cell of a stored segment
-            o[i].x = act ? c[i].x + q4 * L[i].x : (R)0;
-            o[i].y = act ? c[i].y + q4 * L[i].y : (R)0;
+            o[i] = act ? axpy(c[i], q4, L[i]) : czero<CT>();
         }
         st4(a.tmp + idx, o);
     });
 }
 
-template <typename R, int BX, int BY, int BZ, bool CG>
-__device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView &G, int64_t b, int64_t next,
-                                            WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, double &acc)
+template <typename R, typename CT, int BX, int BY, int BZ, bool CG>
+__device__ __forceinline__ void itp_brick_b(const ItpArgs<R, CT> &a, const GridView &G, int64_t b, int64_t next,
+                                            WarpSpace<CT, BX, BY, BZ> &ws, double &acc)
 {
-    using CT = typename Cx<R>::T;
     const R hg = a.g * a.dt / (R)2;
     const R q4 = a.dt / (R)4;
     brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2, ELoad<R>{a.E},
@@ -394,39 +390,37 @@ __device__ __forceinline__ void itp_brick_b(const ItpArgs<R> &a, const GridView 
         CT o[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            o[i].x = c[i].x + q4 * L[i].x;
-            o[i].y = c[i].y + q4 * L[i].y;
-            const R f = p.e[i] >= (R)0 ? p.e[i] * ((R)1 - hg * (o[i].x * o[i].x + o[i].y * o[i].y)) : (R)0;
-            o[i].x *= f;
-            o[i].y *= f;
-            acc += (double)(o[i].x * o[i].x + o[i].y * o[i].y);
+            o[i] = axpy(c[i], q4, L[i]);
+            const R f = p.e[i] >= (R)0 ? p.e[i] * ((R)1 - hg * norm2(o[i])) : (R)0;
+            o[i] = scale(o[i], f);
+            acc += (double)norm2(o[i]);
         }
         st4(a.psi + idx, o);
     });
 }
 
-template <typename R, int BX, int BY, int BZ>
-__global__ void GPE_BOUNDS(R) k_itp_a(const ItpArgs<R> a, const GridView G)
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
+__global__ void GPE_BOUNDS(R) k_itp_a(const ItpArgs<R, CT> a, const GridView G)
 {
     constexpr int NW = KernelCfg<R>::NW;
-    auto &ws = warp_space<R, BX, BY, BZ>();
+    auto &ws = warp_space<R, BX, BY, BZ, CT>();
     const int warp = threadIdx.x >> 5;
     const R sc = (R)a.scalars[0];
     const int64_t stride = (int64_t)gridDim.x * NW;
     for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride)
-        itp_brick_a<R, BX, BY, BZ, false>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, sc);
+        itp_brick_a<R, CT, BX, BY, BZ, false>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, sc);
 }
 
-template <typename R, int BX, int BY, int BZ>
-__global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R> a, const GridView G, double *partials, unsigned int *counter)
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
+__global__ void GPE_BOUNDS(R) k_itp_b(const ItpArgs<R, CT> a, const GridView G, double *partials, unsigned int *counter)
 {
     constexpr int NW = KernelCfg<R>::NW;
-    auto &ws = warp_space<R, BX, BY, BZ>();
+    auto &ws = warp_space<R, BX, BY, BZ, CT>();
     const int warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
     const int64_t stride = (int64_t)gridDim.x * NW;
     for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride)
-        itp_brick_b<R, BX, BY, BZ, false>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, acc[0]);
+        itp_brick_b<R, CT, BX, BY, BZ, false>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, acc[0]);
     double tot[1];
     if (reduce_finish<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         const double nrm = tot[0] * a.dV;
@@ -452,13 +446,13 @@ __global__ void GPE_BOUNDS(R) k_itp_wave(const ItpArgs<R> a, const GridView G, c
         const int64_t b1 = b0 + w.cb < G.nb ? b0 + w.cb : G.nb;
         if (st == 0) {
             for (int64_t b = b0 + warp; b < b1; b += NW)
-                itp_brick_a<R, BX, BY, BZ, true>(a, G, b, b + NW < b1 ? b + NW : -1, ws, sc);
+                itp_brick_a<R, typename Cx<R>::T, BX, BY, BZ, true>(a, G, b, b + NW < b1 ? b + NW : -1, ws, sc);
             publish(w, st, c);
             continue;
         }
         double acc = 0.0;
         for (int64_t b = b0 + warp; b < b1; b += NW)
-            itp_brick_b<R, BX, BY, BZ, true>(a, G, b, b + NW < b1 ? b + NW : -1, ws, acc);
+            itp_brick_b<R, typename Cx<R>::T, BX, BY, BZ, true>(a, G, b, b + NW < b1 ? b + NW : -1, ws, acc);
         const double part = block_sum(acc);
         if (threadIdx.x == 0) chunk_norm[c] = part;
         publish(w, st, c);
@@ -488,17 +482,13 @@ __global__ void k_apply_scale(CT *psi, int64_t n, const double *scalars)
 {
     const double sc = scalars[0];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-        CT v = psi[s];
-        v.x = v.x * sc;
-        v.y = v.y * sc;
-        psi[s] = v;
+        psi[s] = scale(psi[s], sc);
     }
 }
 
 // ------------------------------------------------------------ observables
-template <typename R>
+template <typename R, typename CT = typename Cx<R>::T>
 struct ObsArgs {
-    using CT = typename Cx<R>::T;
     const CT *psi;
     const R *V0;
     const R *V1;
@@ -510,12 +500,11 @@ struct ObsArgs {
     gpe_obs *out;
 };
 
-template <typename R, int BX, int BY, int BZ>
-__global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R> a, const GridView G)
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
+__global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R, CT> a, const GridView G)
 {
-    using CT = typename Cx<R>::T;
     constexpr int NW = KernelCfg<R>::NW;
-    auto &ws = warp_space<R, BX, BY, BZ>();
+    auto &ws = warp_space<R, BX, BY, BZ, CT>();
     const int warp = threadIdx.x >> 5;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // norm, ekin, epot, eint, nonfinite
     const int64_t stride = (int64_t)gridDim.x * NW;
@@ -529,12 +518,12 @@ __global__ void GPE_BOUNDS(R) k_obs(const ObsArgs<R> a, const GridView G)
             for (int i = 0; i < 4; ++i) {
                 if (!(V0[i] < (R)INFINITY)) continue;
                 const R V = a.V1 ? ((R)1 - a.s) * V0[i] + a.s * V1[i] : V0[i];
-                const R rho = c[i].x * c[i].x + c[i].y * c[i].y;
+                const R rho = norm2(c[i]);
                 acc[0] += (double)rho;
-                acc[1] += (double)((R)(-0.5) * (c[i].x * L[i].x + c[i].y * L[i].y));
+                acc[1] += (double)((R)(-0.5) * dotre(c[i], L[i]));
                 acc[2] += (double)(V * rho);
                 acc[3] += (double)((R)0.5 * a.g * rho * rho);
-                acc[4] += (isfinite(c[i].x) && isfinite(c[i].y)) ? 0.0 : 1.0;
+                acc[4] += finite_v(c[i]) ? 0.0 : 1.0;
             }
         });
     }
@@ -618,7 +607,7 @@ const void *potential_ptr(gpe_state *st, int slot)
 {
     gpe_grid *g = st->grid;
     if (!g->d_V[slot]) return nullptr;
-    if (st->dtype == GPE_C128) return g->d_V[slot];
+    if (st->dtype == GPE_C128 || st->dtype == GPE_R64) return g->d_V[slot];
     if (ensure_vf(g, slot) != GPE_OK) return nullptr;
     return g->d_Vf[slot];
 }
@@ -1151,17 +1140,16 @@ static int rkgen_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, do
     return GPE_OK;
 }
 
-template <typename R, int BX, int BY, int BZ>
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
 static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cudaStream_t s)
 {
-    using CT = typename Cx<R>::T;
     const gpe_grid *g = st->grid;
     if (st->E_dt != p->dt) {
         k_make_E<R><<<g->nsm * 8, 256, 0, s>>>(g->d_V[0], (R *)st->d_E, g->n_packed, p->dt);
         GPE_LAUNCH_CHECK();
         st->E_dt = p->dt;
     }
-    ItpArgs<R> a{};
+    ItpArgs<R, CT> a{};
     a.psi = (CT *)st->d_psi;
     a.tmp = (CT *)st->d_work[0];
     a.E = (const R *)st->d_E;
@@ -1177,8 +1165,9 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
     GPE_LAUNCH_CHECK();
     const GridView G = view(g);
     const int th = KernelCfg<R>::THREADS;
-    const size_t smem = smem_bytes<R, BX, BY, BZ>();
-    if (g->sched == GPE_SCHED_WAVE || g->sched == GPE_SCHED_WAVE2) {
+    const size_t smem = smem_bytes<R, BX, BY, BZ, CT>();
+    // real-valued states run the staged schedule whatever the grid's
+    if constexpr (is_cplx<CT>()) if (g->sched == GPE_SCHED_WAVE || g->sched == GPE_SCHED_WAVE2) {
         GPE_TRY(ensure_wave(st));
         auto k = k_itp_wave<R, BX, BY, BZ>;
         const int nblk = (int)std::min<int64_t>((int64_t)g->nsm * per_sm_for(k, th, smem), 2 * g->n_chunks);
@@ -1187,9 +1176,13 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
             GPE_LAUNCH_CHECK();
             advance_wave(st, 2, nblk, true);
         }
-    } else {
-        auto ka = k_itp_a<R, BX, BY, BZ>;
-        auto kb = k_itp_b<R, BX, BY, BZ>;
+        k_apply_scale<CT><<<g->nsm * 8, 256, 0, s>>>((CT *)st->d_psi, g->n_packed, st->red.scalars);
+        GPE_LAUNCH_CHECK();
+        return GPE_OK;
+    }
+    {
+        auto ka = k_itp_a<R, BX, BY, BZ, CT>;
+        auto kb = k_itp_b<R, BX, BY, BZ, CT>;
         const int nba = blocks_for<R>(ka, g, smem), nbb = blocks_for<R>(kb, g, smem);
         auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
             for (int64_t n = 0; n < cnt; ++n) {
@@ -1216,13 +1209,13 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
     return GPE_OK;
 }
 
-template <typename R, int BX, int BY, int BZ>
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
 static int obs_run(const gpe_state *stc, double gg, double sb, cudaStream_t s)
 {
     gpe_state *st = const_cast<gpe_state *>(stc);
     const gpe_grid *g = st->grid;
-    ObsArgs<R> a{};
-    a.psi = (const typename Cx<R>::T *)st->d_psi;
+    ObsArgs<R, CT> a{};
+    a.psi = (const CT *)st->d_psi;
     a.V0 = (const R *)potential_ptr(st, 0);
     a.V1 = (sb != 0.0) ? (const R *)potential_ptr(st, 1) : nullptr;
     if (sb != 0.0 && !a.V1) return fail(GPE_ERR_ARG, "s_blend != 0 needs potential slot 1");
@@ -1235,12 +1228,36 @@ static int obs_run(const gpe_state *stc, double gg, double sb, cudaStream_t s)
     a.partials = st->red.partials;
     a.counter = st->red.counter;
     a.out = (gpe_obs *)(st->red.scalars + 2);
-    const size_t smem = smem_bytes<R, BX, BY, BZ>();
-    auto k = k_obs<R, BX, BY, BZ>;
+    const size_t smem = smem_bytes<R, BX, BY, BZ, CT>();
+    auto k = k_obs<R, BX, BY, BZ, CT>;
     k<<<blocks_for<R>(k, g, smem), KernelCfg<R>::THREADS, smem, s>>>(a, view(g));
     GPE_LAUNCH_CHECK();
     return GPE_OK;
 }
+
+// dense <-> packed copy in the state's value type
+template <bool STORE>
+static void dense_io(const gpe_state *st, void *dense, const GridView &G, const BoxI &bi, cudaStream_t s)
+{
+    const gpe_grid *g = st->grid;
+    const int nb = g->nsm * 8;
+    switch (st->dtype) {
+    case GPE_C128:
+        k_dense_io<double2, STORE><<<nb, 256, 0, s>>>((double2 *)st->d_psi, (double2 *)dense, g->d_org, g->d_mask, G, g->n_stored, bi);
+        break;
+    case GPE_C64:
+        k_dense_io<float2, STORE><<<nb, 256, 0, s>>>((float2 *)st->d_psi, (float2 *)dense, g->d_org, g->d_mask, G, g->n_stored, bi);
+        break;
+    case GPE_R64:
+        k_dense_io<double, STORE><<<nb, 256, 0, s>>>((double *)st->d_psi, (double *)dense, g->d_org, g->d_mask, G, g->n_stored, bi);
+        break;
+    default:
+        k_dense_io<float, STORE><<<nb, 256, 0, s>>>((float *)st->d_psi, (float *)dense, g->d_org, g->d_mask, G, g->n_stored, bi);
+        break;
+    }
+}
+
+static bool is_real_dtype(int dtype) { return dtype == GPE_R64 || dtype == GPE_R32; }
 
 // device error word of the wavefront schedule (0 = fine)
 static int wave_error(const gpe_state *st, cudaStream_t s)
@@ -1262,14 +1279,17 @@ extern "C" int gpe_state_create(gpe_grid *g, int dtype, gpe_state **out)
 {
     if (!g || !out) return fail(GPE_ERR_ARG, "NULL argument");
     *out = nullptr;
-    if (dtype != GPE_C128 && dtype != GPE_C64) return fail(GPE_ERR_ARG, "dtype must be GPE_C128 or GPE_C64");
+    if (dtype != GPE_C128 && dtype != GPE_C64 && dtype != GPE_R64 && dtype != GPE_R32)
+        return fail(GPE_ERR_ARG, "dtype must be GPE_C128, GPE_C64, GPE_R64 or GPE_R32");
     gpe_state *st = new gpe_state();
     st->grid = g;
     st->dtype = dtype;
-    st->elem = dtype == GPE_C128 ? 16 : 8;
+    st->elem = dtype == GPE_C128 ? 16 : (dtype == GPE_R32 ? 4 : 8);
     int rc = dev_alloc(&st->d_psi, g->n_packed * st->elem);
     if (rc == GPE_OK) rc = dev_zero(st->d_psi, g->n_packed * st->elem);
-    if (rc == GPE_OK) rc = dev_alloc(&st->d_E, g->n_packed * st->elem / 2);
+    // E = exp(-V dt/2) in the state's real type (8 bytes for C128 and R64)
+    const size_t real_bytes = (dtype == GPE_C128 || dtype == GPE_R64) ? 8 : 4;
+    if (rc == GPE_OK) rc = dev_alloc(&st->d_E, g->n_packed * real_bytes);
     if (rc == GPE_OK) rc = dev_alloc_t(&st->d_clock, 1);
     if (rc == GPE_OK) rc = red_alloc(st->red, g->nsm * 32);
     if (rc == GPE_OK && cudaMallocHost(&st->h_obs, sizeof(gpe_obs)) != cudaSuccess)
@@ -1360,10 +1380,12 @@ extern "C" int gpe_state_load(gpe_state *st, const void *psi, int layout, int on
     if (layout == GPE_LAYOUT_COMPACT) {
         GPE_TRY_CUDA(cudaMemcpyAsync(st->d_psi, psi, g->n_packed * st->elem,
                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        if (st->dtype == GPE_C128)
-            k_zero_inactive<double2><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, g->d_V[0], g->n_packed);
-        else
-            k_zero_inactive<float2><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, g->d_V[0], g->n_packed);
+        switch (st->dtype) {
+        case GPE_C128: k_zero_inactive<double2><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, g->d_V[0], g->n_packed); break;
+        case GPE_C64: k_zero_inactive<float2><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, g->d_V[0], g->n_packed); break;
+        case GPE_R64: k_zero_inactive<double><<<g->nsm * 8, 256, 0, s>>>((double *)st->d_psi, g->d_V[0], g->n_packed); break;
+        default: k_zero_inactive<float><<<g->nsm * 8, 256, 0, s>>>((float *)st->d_psi, g->d_V[0], g->n_packed); break;
+        }
         GPE_LAUNCH_CHECK();
         if (!on_device) GPE_TRY_CUDA(cudaStreamSynchronize(s));
         return GPE_OK;
@@ -1384,12 +1406,7 @@ extern "C" int gpe_state_load(gpe_state *st, const void *psi, int layout, int on
     }
     cudaError_t e = cudaMemsetAsync(st->d_psi, 0, g->n_packed * st->elem, s);
     if (e == cudaSuccess) {
-        if (st->dtype == GPE_C128)
-            k_dense_io<double2, false><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, (double2 *)src, g->d_org, g->d_mask, G,
-                                                                 g->n_stored, bi);
-        else
-            k_dense_io<float2, false><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, (float2 *)src, g->d_org, g->d_mask, G,
-                                                                g->n_stored, bi);
+        dense_io<false>(st, const_cast<void *>(src), G, bi, s);
         count_launch();
         e = cudaGetLastError();
     }
@@ -1426,12 +1443,7 @@ extern "C" int gpe_state_store(const gpe_state *st, void *psi, int layout, int o
     const GridView G = view(g);
     cudaError_t e = cudaMemsetAsync(dst, 0, dbytes, s);
     if (e == cudaSuccess) {
-        if (st->dtype == GPE_C128)
-            k_dense_io<double2, true><<<g->nsm * 8, 256, 0, s>>>((double2 *)st->d_psi, (double2 *)dst, g->d_org, g->d_mask, G,
-                                                                g->n_stored, bi);
-        else
-            k_dense_io<float2, true><<<g->nsm * 8, 256, 0, s>>>((float2 *)st->d_psi, (float2 *)dst, g->d_org, g->d_mask, G,
-                                                               g->n_stored, bi);
+        dense_io<true>(st, dst, G, bi, s);
         count_launch();
         e = cudaGetLastError();
     }
@@ -1459,6 +1471,7 @@ extern "C" int gpe_state_copy(gpe_state *dst, const gpe_state *src, gpe_stream s
 extern "C" int gpe_step_real(gpe_state *st, const gpe_real_params *p, int64_t nsteps, double t0, gpe_stream stream)
 {
     GPE_TRY(check_state(st));
+    if (is_real_dtype(st->dtype)) return fail(GPE_ERR_ARG, "real-time steps need a complex state");
     if (!p) return fail(GPE_ERR_ARG, "params is NULL");
     if (nsteps < 0) return fail(GPE_ERR_ARG, "nsteps < 0");
     if (p->integrator != GPE_RK4 && p->integrator != GPE_RKHE3 && p->integrator != GPE_RKCK)
@@ -1511,9 +1524,15 @@ extern "C" int gpe_step_imag(gpe_state *st, const gpe_imag_params *p, int64_t ns
     if (nsteps == 0) return GPE_OK;
     GPE_TRY(ensure_work(st, 1));
     cudaStream_t s = S(stream);
-    const bool c128 = st->dtype == GPE_C128;
-#define ITP_CASE(id, X, Y, Z) \
-    case id: return c128 ? itp_run<double, X, Y, Z>(st, p, nsteps, s) : itp_run<float, X, Y, Z>(st, p, nsteps, s);
+    const int dt_ = st->dtype;
+#define ITP_CASE(id, X, Y, Z)                                                                         \
+    case id:                                                                                          \
+        switch (dt_) {                                                                                \
+        case GPE_C128: return itp_run<double, X, Y, Z>(st, p, nsteps, s);                             \
+        case GPE_C64: return itp_run<float, X, Y, Z>(st, p, nsteps, s);                               \
+        case GPE_R64: return itp_run<double, X, Y, Z, double>(st, p, nsteps, s);                      \
+        default: return itp_run<float, X, Y, Z, float>(st, p, nsteps, s);                             \
+        }
     switch (st->grid->shape) { GPE_SHAPES(ITP_CASE) }
 #undef ITP_CASE
     return fail(GPE_ERR_STATE, "bad brick shape");
@@ -1525,10 +1544,17 @@ extern "C" int gpe_observables(const gpe_state *st, double g, double s_blend, gp
     if (!out) return fail(GPE_ERR_ARG, "out is NULL");
     if (!std::isfinite(g) || !std::isfinite(s_blend)) return fail(GPE_ERR_ARG, "g and s_blend must be finite");
     cudaStream_t s = S(stream);
-    const bool c128 = st->dtype == GPE_C128;
+    const int dt_ = st->dtype;
     int rc = GPE_ERR_STATE;
-#define OBS_CASE(id, X, Y, Z) \
-    case id: rc = c128 ? obs_run<double, X, Y, Z>(st, g, s_blend, s) : obs_run<float, X, Y, Z>(st, g, s_blend, s); break;
+#define OBS_CASE(id, X, Y, Z)                                                         \
+    case id:                                                                          \
+        switch (dt_) {                                                                \
+        case GPE_C128: rc = obs_run<double, X, Y, Z>(st, g, s_blend, s); break;       \
+        case GPE_C64: rc = obs_run<float, X, Y, Z>(st, g, s_blend, s); break;         \
+        case GPE_R64: rc = obs_run<double, X, Y, Z, double>(st, g, s_blend, s); break; \
+        default: rc = obs_run<float, X, Y, Z, float>(st, g, s_blend, s); break;       \
+        }                                                                             \
+        break;
     switch (st->grid->shape) { GPE_SHAPES(OBS_CASE) }
 #undef OBS_CASE
     if (rc != GPE_OK) return rc;
@@ -1546,6 +1572,7 @@ extern "C" int gpe_overlap(const gpe_state *a, const gpe_state *b, double out[2]
     GPE_TRY(check_state(b));
     if (!out) return fail(GPE_ERR_ARG, "out is NULL");
     if (a->grid != b->grid || a->dtype != b->dtype) return fail(GPE_ERR_ARG, "states differ in grid or dtype");
+    if (is_real_dtype(a->dtype)) return fail(GPE_ERR_ARG, "the overlap is computed for complex states");
     const gpe_grid *g = a->grid;
     cudaStream_t s = S(stream);
     gpe_state *w = const_cast<gpe_state *>(a);

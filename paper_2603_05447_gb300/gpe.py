@@ -38,7 +38,7 @@ GPE_ORDER_ZMAJOR, GPE_ORDER_MORTON = 0, 1
 GPE_SCHED_STAGED, GPE_SCHED_WAVE, GPE_SCHED_WAVE2 = 0, 1, 2
 GPE_F64, GPE_F32 = 1, 2
 GPE_POT_HARMONIC, GPE_POT_ELLIPSOID_SHELL = 1, 2
-GPE_C128, GPE_C64 = 1, 2
+GPE_C128, GPE_C64, GPE_R64, GPE_R32 = 1, 2, 3, 4
 GPE_LAYOUT_DENSE, GPE_LAYOUT_COMPACT = 0, 1
 GPE_RK4, GPE_RKHE3, GPE_RKCK = 0, 1, 2
 GPE_V_STATIC, GPE_V_BLEND = 0, 1
