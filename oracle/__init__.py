@@ -56,6 +56,12 @@ def _load():
         lib.orc_neighbors.restype = ctypes.c_int
         lib.orc_neighbors.argtypes = [ctypes.c_int64, _c_i64p, ctypes.c_int64,
                                       ctypes.c_int64, ctypes.c_int64, _c_i64p]
+        lib.orc_edge_neighbors.restype = ctypes.c_int
+        lib.orc_edge_neighbors.argtypes = [ctypes.c_int64, _c_i64p, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.c_int64, _c_i64p]
+        lib.orc_laplacian19.restype = None
+        lib.orc_laplacian19.argtypes = ([ctypes.c_int64, _c_i64p, _c_i64p] + [ctypes.c_double] * 3
+                                        + [_c_f64p, _c_f64p])
         lib.orc_laplacian.restype = None
         lib.orc_laplacian.argtypes = [ctypes.c_int64, _c_i64p] + [ctypes.c_double] * 3 + [_c_f64p, _c_f64p]
         lib.orc_rhs_real.restype = None
@@ -137,12 +143,81 @@ class Grid:
         c = self.cells
         return np.stack([c % self.nx, (c // self.nx) % self.ny, c // (self.nx * self.ny)], axis=1)
 
+    @property
+    def nbr_e(self) -> np.ndarray:
+        """Edge-neighbour table (n, 12) of the 19-point stencil, built on first use."""
+        if not hasattr(self, "_nbr_e"):
+            e = np.empty((self.n, 12), dtype=np.int64)
+            assert _load().orc_edge_neighbors(self.n, _pi64(self.cells), self.nx, self.ny, self.nz, _pi64(e)) == 0
+            self._nbr_e = e
+        return self._nbr_e
 
-def laplacian(grid: Grid, psi: np.ndarray) -> np.ndarray:
+
+def laplacian(grid: Grid, psi: np.ndarray, stencil: int = 7) -> np.ndarray:
+    """The 7-point (Eq. (B1)) or 19-point (App. B) Laplacian on the active cells."""
     psi, pp = _cvec(psi)
     out = np.empty(grid.n, dtype=np.complex128)
-    _load().orc_laplacian(grid.n, _pi64(grid.nbr), *grid.h, pp, out.view(np.float64).ctypes.data_as(_c_f64p))
+    op = out.view(np.float64).ctypes.data_as(_c_f64p)
+    if stencil == 7:
+        _load().orc_laplacian(grid.n, _pi64(grid.nbr), *grid.h, pp, op)
+    elif stencil == 19:
+        _load().orc_laplacian19(grid.n, _pi64(grid.nbr), _pi64(grid.nbr_e), *grid.h, pp, op)
+    else:
+        raise ValueError("stencil must be 7 or 19")
     return out
+
+
+# --- steps with either stencil, in numpy on top of the C Laplacian --------
+# (the C step functions use the 7-point stencil; these restate the same
+#  steps with the Laplacian as a parameter, for the 19-point stencil)
+def _V_at(V0, V1, knots, T, t):
+    if V1 is None or knots is None:
+        return V0
+    s = ramp_s(knots, T, t)
+    return (1.0 - s) * V0 + s * V1
+
+
+def rhs(grid: Grid, V, g, y, stencil: int = 7) -> np.ndarray:
+    """f(y) = -i (T + V + g|y|^2) y, T = -1/2 Laplacian (Eq. (8))."""
+    y = np.asarray(y, dtype=np.complex128)
+    return -1j * (-0.5 * laplacian(grid, y, stencil) + (V + g * np.abs(y) ** 2) * y)
+
+
+def rk_step_np(grid: Grid, V0, psi, g, t, dt, method="RK4", V1=None, knots=None, T=0.0,
+               stencil: int = 7) -> np.ndarray:
+    """Butcher-form explicit RK step (TABLEAUX[method]) in numpy."""
+    A, b, c = TABLEAUX[method]
+    y0 = np.asarray(psi, dtype=np.complex128)
+    k = []
+    for i in range(len(b)):
+        yi = y0 + dt * sum((A[i, j] * k[j] for j in range(i)), np.zeros_like(y0))
+        k.append(rhs(grid, _V_at(V0, V1, knots, T, t + c[i] * dt), g, yi, stencil))
+    return y0 + dt * sum(b[i] * k[i] for i in range(len(b)))
+
+
+def itp_step_np(grid: Grid, V, psi, g, dt, N=1.0, stencil: int = 7):
+    """The imaginary-time step in the paper's order (Eqs. (6)-(7)) in numpy;
+    returns (new psi, norm before renormalisation)."""
+    y = np.asarray(psi, dtype=np.complex128)
+    E = np.exp(-V * dt / 2.0)
+    y = y * E * (1.0 - g * np.abs(y) ** 2 * dt / 2.0)
+    for _ in range(2):
+        y = y - (dt / 2.0) * (-0.5 * laplacian(grid, y, stencil))
+    y = y * E * (1.0 - g * np.abs(y) ** 2 * dt / 2.0)
+    nrm = float(np.sum(np.abs(y) ** 2) * grid.dV)
+    return y * np.sqrt(N / nrm), nrm
+
+
+def observables_np(grid: Grid, V, g, psi, stencil: int = 7) -> dict:
+    y = np.asarray(psi, dtype=np.complex128)
+    rho = np.abs(y) ** 2
+    Ty = -0.5 * laplacian(grid, y, stencil)
+    norm = float(np.sum(rho) * grid.dV)
+    e_kin = float(np.sum(np.real(np.conj(y) * Ty)) * grid.dV)
+    e_pot = float(np.sum(V * rho) * grid.dV)
+    e_int = float(np.sum(0.5 * g * rho ** 2) * grid.dV)
+    return dict(norm=norm, energy=e_kin + e_pot + e_int, mu=(e_kin + e_pot + 2 * e_int) / norm,
+                e_kin=e_kin, e_pot=e_pot, e_int=e_int)
 
 
 def rhs_real(grid: Grid, V: np.ndarray, g: float, y: np.ndarray) -> np.ndarray:

@@ -100,6 +100,63 @@ void orc_laplacian(int64_t n, const int64_t *nbr, double hx, double hy,
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Edge neighbours for the 19-point stencil: for every active cell the  */
+/* 12 cells that differ by one step along two axes, in the order        */
+/* xy: (-1,-1,0) (+1,-1,0) (-1,+1,0) (+1,+1,0);                         */
+/* xz: (-1,0,-1) (+1,0,-1) (-1,0,+1) (+1,0,+1);                         */
+/* yz: (0,-1,-1) (0,+1,-1) (0,-1,+1) (0,+1,+1);  -1 when absent.        */
+/* ------------------------------------------------------------------ */
+int orc_edge_neighbors(int64_t n, const int64_t *cells, int64_t nx, int64_t ny,
+                       int64_t nz, int64_t *nbr_e)
+{
+    static const int64_t d[12][3] = {{-1,-1,0},{1,-1,0},{-1,1,0},{1,1,0},
+                                     {-1,0,-1},{1,0,-1},{-1,0,1},{1,0,1},
+                                     {0,-1,-1},{0,1,-1},{0,-1,1},{0,1,1}};
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+        int64_t lin = cells[c];
+        int64_t i = lin % nx, j = (lin / nx) % ny, k = lin / (nx * ny);
+        for (int e = 0; e < 12; ++e) {
+            int64_t ii = i + d[e][0], jj = j + d[e][1], kk = k + d[e][2];
+            int64_t r = -1;
+            if (ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz)
+                r = find_cell(n, cells, ii + nx * (jj + ny * kk));
+            nbr_e[12 * c + e] = r;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 19-point higher-order compact Laplacian for unequal spacings (App. B):*/
+/*   L19 = L7 + 1/12 [ (hx^2+hy^2) dx2 dy2 + (hx^2+hz^2) dx2 dz2         */
+/*                    + (hy^2+hz^2) dy2 dz2 ],                           */
+/* dx2 dy2 psi = (sum of the 4 xy-edge cells - 2 (sum of the 4 xy face  */
+/* cells) + 4 psi) / (hx^2 hy^2), and likewise for xz and yz.            */
+/* ------------------------------------------------------------------ */
+void orc_laplacian19(int64_t n, const int64_t *nbr, const int64_t *nbr_e, double hx,
+                     double hy, double hz, const cplx *psi, cplx *out)
+{
+    const double h2[3] = {hx * hx, hy * hy, hz * hz};
+    orc_laplacian(n, nbr, hx, hy, hz, psi, out);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+        cplx mixed = 0.0;
+        for (int p = 0; p < 3; ++p) {            /* planes xy, xz, yz */
+            const int a = p == 2 ? 1 : 0;        /* first axis of the plane */
+            const int b = p == 0 ? 1 : 2;        /* second axis */
+            cplx edges = 0.0;
+            for (int q = 0; q < 4; ++q) edges += val(psi, nbr_e[12 * c + 4 * p + q]);
+            cplx faces = val(psi, nbr[6 * c + 2 * a]) + val(psi, nbr[6 * c + 2 * a + 1]) +
+                         val(psi, nbr[6 * c + 2 * b]) + val(psi, nbr[6 * c + 2 * b + 1]);
+            cplx d2d2 = (edges - 2.0 * faces + 4.0 * psi[c]) / (h2[a] * h2[b]);
+            mixed += (h2[a] + h2[b]) * d2d2;
+        }
+        out[c] += mixed / 12.0;
+    }
+}
+
 /* H psi = (T + V + g|psi|^2) psi with T = -1/2 Laplacian (Eq. (2)). */
 static void apply_H(int64_t n, const int64_t *nbr, const double h[3],
                     const double *V, double g, const cplx *psi, cplx *out)

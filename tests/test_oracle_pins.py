@@ -561,3 +561,65 @@ def test_appendix_A_memory_optimized_recurrence_equals_butcher_step(oracle_mod, 
     y1 = sum(b_star[j] * Y[j] for j in range(n)) + dt * b[n - 1] * f(t + c[n - 1] * dt, Y[n - 1])
     ref = oracle_mod.rk_step(g, V0, y0, gg, t, dt, method, V1, knots, T)
     assert relerr(y1, ref) < 1e-13
+
+
+# ----------------------------------------------------------------- 19-point stencil (App. B)
+def kron_laplacian19(nx, ny, nz, h):
+    """App. B written out with Kronecker products: the 7-point sum plus
+    1/12 [(hx^2+hy^2) d2x d2y + (hx^2+hz^2) d2x d2z + (hy^2+hz^2) d2y d2z]."""
+    def d2(n, hh):
+        return sp.diags([np.ones(n - 1), -2 * np.ones(n), np.ones(n - 1)], [-1, 0, 1]) / hh ** 2
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    Dx, Dy, Dz = d2(nx, h[0]), d2(ny, h[1]), d2(nz, h[2])
+    hx2, hy2, hz2 = h[0] ** 2, h[1] ** 2, h[2] ** 2
+    mixed = ((hx2 + hy2) * sp.kron(Iz, sp.kron(Dy, Dx)) + (hx2 + hz2) * sp.kron(Dz, sp.kron(Iy, Dx))
+             + (hy2 + hz2) * sp.kron(Dz, sp.kron(Dy, Ix)))
+    return (kron_laplacian(nx, ny, nz, h) + mixed / 12.0).tocsr()
+
+
+@pytest.mark.parametrize("frac", [1.0, 0.6])
+def test_laplacian19_equals_appendix_B_kronecker_form_with_deleted_rows(oracle_mod, frac):
+    h = (0.21, 0.34, 0.47)
+    mask = random_mask((9, 8, 10), frac, 61)
+    g = oracle_mod.Grid(mask, h)
+    L = kron_laplacian19(g.nx, g.ny, g.nz, h)[g.cells][:, g.cells]
+    psi = cvec(g.n, 62)
+    assert relerr(oracle_mod.laplacian(g, psi, 19), L @ psi) < 1e-14
+
+
+def test_laplacian19_exact_on_quadratics_kills_constants_and_differs_from_7pt(oracle_mod):
+    """The mixed differences vanish on polynomials of degree <= 2 (so the
+    19-point stencil is exact there, like the 7-point one) but not on x^2 y^2."""
+    box = inputs.Box(12, 11, 10, 0.2, 0.3, 0.4)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.96, 63), (box.hx, box.hy, box.hz))
+    x, y, z = box.coords_of(g.ijk())
+    full = np.all(g.nbr >= 0, axis=1) & np.all(g.nbr_e >= 0, axis=1)
+    assert full.sum() > 10
+    q = (x * x + 2 * y * y + 3 * z * z + x * y - y * z).astype(np.complex128)
+    assert np.allclose(oracle_mod.laplacian(g, q, 19)[full], 12.0, rtol=0, atol=1e-9)
+    const = np.full(g.n, 1.0 + 2.0j)
+    assert np.allclose(oracle_mod.laplacian(g, const, 19)[full], 0.0, atol=1e-10)
+    p = (x * x * y * y).astype(np.complex128)
+    diff = oracle_mod.laplacian(g, p, 19) - oracle_mod.laplacian(g, p, 7)
+    # d2x d2y (x^2 y^2) = 4 exactly: the extra term is (hx^2 + hy^2) * 4 / 12
+    assert np.allclose(diff[full], (box.hx ** 2 + box.hy ** 2) * 4 / 12, rtol=1e-9, atol=0)
+
+
+def test_numpy_steps_equal_the_c_steps(oracle_mod):
+    """The numpy restatements (used with the 19-point stencil) reproduce the
+    C steps with the 7-point stencil."""
+    box = inputs.Box(6, 7, 5, 0.3, 0.32, 0.34)
+    g = oracle_mod.Grid(random_mask(box.shape, 0.8, 64), (box.hx, box.hy, box.hz))
+    rng = np.random.default_rng(65)
+    V0, V1 = rng.uniform(0, 3, g.n), rng.uniform(0, 3, g.n)
+    psi = cvec(g.n, 66) * 0.3
+    knots = np.array([0.1, 0.5, 0.9])
+    a = oracle_mod.rk_step_np(g, V0, psi, 3.0, 0.02, 0.003, "RK4", V1, knots, 0.2)
+    b = oracle_mod.rk4_step(g, V0, psi, 3.0, 0.02, 0.003, V1, knots, 0.2)
+    assert relerr(a, b) < 1e-14
+    a, na = oracle_mod.itp_step_np(g, V0, psi, 3.0, 0.004, 1.0)
+    b, nb = oracle_mod.itp_step(g, V0, psi, 3.0, 0.004, 1.0)
+    assert relerr(a, b) < 1e-14 and abs(na - nb) < 1e-14 * nb
+    oa, ob = oracle_mod.observables_np(g, V0, 3.0, psi), oracle_mod.observables(g, V0, 3.0, psi)
+    for k in ("norm", "energy", "mu", "e_kin", "e_pot", "e_int"):
+        assert abs(oa[k] - ob[k]) <= 1e-13 * max(1.0, abs(ob[k])), k
