@@ -104,14 +104,19 @@ enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2 };
 
 /* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
  * all three are 0), 8x8x4, 8x4x4.  chunk = bricks per wavefront task
- * (0: about 2048 lattice cells). */
+ * (0: about 2048 lattice cells).  stencil = 7 (default, also 0): the 7-point
+ * Laplacian (Eq. (B1)); 19: the 19-point higher-order compact Laplacian of
+ * App. B, which also reads the 12 edge neighbours of a cell.  A 19-point grid
+ * runs the staged schedule for gpe_step_real (RK4), gpe_step_imag,
+ * gpe_observables and gpe_ground_state; the other step calls refuse it
+ * (GPE_ERR_ARG). */
 typedef struct gpe_grid_opts {
     int32_t bx, by, bz;
     int32_t mask_mode; /* GPE_MASK_* */
     int32_t order;     /* GPE_ORDER_* : order of the brick list in memory */
     int32_t sched;     /* GPE_SCHED_* */
     int32_t chunk;
-    int32_t reserved;
+    int32_t stencil;   /* 0 or 7, or 19 */
 } gpe_grid_opts;
 
 enum { GPE_F64 = 1, GPE_F32 = 2 };   /* element type of a real input array */

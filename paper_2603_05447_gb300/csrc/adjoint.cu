@@ -231,6 +231,7 @@ extern "C" int gpe_ramp_forward(gpe_state *st, const gpe_real_params *p, int64_t
     if (p->potential != GPE_V_BLEND) return fail(GPE_ERR_ARG, "the ramp gradient needs potential = GPE_V_BLEND");
     if (p->integrator != GPE_RK4) return fail(GPE_ERR_ARG, "the ramp gradient is the adjoint of the RK4 step");
     if (st->dtype != GPE_C128 && st->dtype != GPE_C64) return fail(GPE_ERR_ARG, "the ramp gradient needs a complex state");
+    if (st->grid->stencil != 7) return fail(GPE_ERR_ARG, "the ramp gradient is built for the 7-point stencil");
     const gpe_grid *g = st->grid;
     const size_t bytes = (size_t)g->n_packed * st->elem;
     gpe_tape *t = new gpe_tape();

@@ -289,6 +289,8 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
         if (states[i]->dtype != dtype || states[i]->grid->shape != shape)
             return fail(GPE_ERR_ARG, "batch states must share dtype and brick shape (state %d differs)", i);
     if (dtype != GPE_C128 && dtype != GPE_C64) return fail(GPE_ERR_ARG, "batches hold complex states");
+    for (int i = 0; i < n; ++i)
+        if (states[i]->grid->stencil != 7) return fail(GPE_ERR_ARG, "batches run the 7-point stencil (state %d)", i);
     gpe_batch *B = new gpe_batch();
     B->n = n;
     B->dtype = dtype;

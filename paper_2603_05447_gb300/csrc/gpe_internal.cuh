@@ -79,6 +79,11 @@ struct BrickRec {
 // per brick: its record followed by its six face neighbours' (-x +x -y +y -z
 // +z; empty records for absent neighbours), built on the host
 void build_rec7(const std::vector<BrickRec> &rec, const std::vector<int32_t> &nbr, std::vector<BrickRec> &out);
+// records of each brick, its 6 face and 12 edge neighbours (edge order: xy
+// (-1,-1,0) (+1,-1,0) (-1,+1,0) (+1,+1,0); xz (-1,0,-1) (+1,0,-1) (-1,0,+1)
+// (+1,0,+1); yz (0,-1,-1) (0,+1,-1) (0,-1,+1) (0,+1,+1))
+void build_rec19(const std::vector<BrickRec> &rec, const std::vector<int32_t> &nbr,
+                 const std::vector<int32_t> &nbr_e, std::vector<BrickRec> &out);
 
 // packed index of the first cell of segment q, if stored
 __host__ __device__ __forceinline__ bool seg_index(const BrickRec &r, int q, uint32_t &idx)
@@ -295,6 +300,8 @@ struct gpe_grid {
     uint32_t *d_mask = nullptr;
     gpe::BrickRec *d_rec = nullptr;
     gpe::BrickRec *d_rec7 = nullptr;  // [nb*7] record of each brick and of its six face neighbours
+    gpe::BrickRec *d_rec19 = nullptr; // [nb*19] ... and of its 12 edge neighbours (19-point grids)
+    int stencil = 7;                  // 7 or 19 points
     int32_t *d_bvol = nullptr;  // brick-grid volume nbx*nby*nbz -> brick id or -1
     double *d_V[2] = {nullptr, nullptr};
     float *d_Vf[2] = {nullptr, nullptr};  // float copies, made on first use
@@ -345,6 +352,10 @@ struct gpe_state {
 
 namespace gpe {
 int ensure_work(gpe_state *st, int n);          // allocate d_work[0..n-1] (zeroed)
+// step drivers of 19-point grids (step19.cu)
+int rk4_run19(gpe_state *st, const gpe_real_params *p, int64_t nsteps, double t0, cudaStream_t s);
+int itp_run19(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cudaStream_t s);
+int obs_run19(const gpe_state *st, double g, double s_blend, cudaStream_t s);
 int ensure_vf(gpe_grid *g, int slot);           // float copy of a potential slot
 const void *potential_ptr(gpe_state *st, int slot);  // V slot in state precision
 int launch_blocks(const gpe_grid *g, int threads, int per_sm);

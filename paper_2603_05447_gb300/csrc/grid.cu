@@ -402,7 +402,37 @@ void gpe::build_rec7(const std::vector<BrickRec> &rec, const std::vector<int32_t
     }
 }
 
+void gpe::build_rec19(const std::vector<BrickRec> &rec, const std::vector<int32_t> &nbr,
+                      const std::vector<int32_t> &nbr_e, std::vector<BrickRec> &out)
+{
+    const size_t nb = rec.size();
+    out.assign(nb * 19, BrickRec{});
+    for (size_t b = 0; b < nb; ++b) {
+        out[19 * b] = rec[b];
+        for (int d = 0; d < 6; ++d)
+            if (nbr[6 * b + d] >= 0) out[19 * b + 1 + d] = rec[nbr[6 * b + d]];
+        for (int e = 0; e < 12; ++e)
+            if (nbr_e[12 * b + e] >= 0) out[19 * b + 7 + e] = rec[nbr_e[12 * b + e]];
+    }
+}
+
 namespace gpe {
+
+// the 12 edge neighbours of each brick (order as in build_rec19), -1 if absent
+__global__ void k_edge_neighbors(int64_t nb, const int32_t *coords, int64_t nbx, int64_t nby, int64_t nbz,
+                                 const int32_t *bvol, int32_t *nbr_e)
+{
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nb) return;
+    const int8_t d[12][3] = {{-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}, {-1, 0, -1}, {1, 0, -1},
+                             {-1, 0, 1},  {1, 0, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+    for (int e = 0; e < 12; ++e) {
+        const int64_t x = coords[3 * id] + d[e][0], y = coords[3 * id + 1] + d[e][1], z = coords[3 * id + 2] + d[e][2];
+        int32_t r = -1;
+        if (x >= 0 && x < nbx && y >= 0 && y < nby && z >= 0 && z < nbz) r = bvol[x + nbx * (y + nby * z)];
+        nbr_e[12 * id + e] = r;
+    }
+}
 
 static BoxD boxd(const gpe_box &b)
 {
@@ -445,6 +475,7 @@ static void grid_free(gpe_grid *g)
     if (!g) return;
     dev_free(g->d_rec);
     dev_free(g->d_rec7);
+    dev_free(g->d_rec19);
     dev_free(g->d_chunk_lohi);
     dev_free(g->d_tasks);
     dev_free(g->d_dep_off);
@@ -476,6 +507,7 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
         return fail(GPE_ERR_ARG, "unknown mask mode %d", o.mask_mode);
     if (o.order != GPE_ORDER_MORTON && o.order != GPE_ORDER_ZMAJOR)
         return fail(GPE_ERR_ARG, "unknown brick order %d", o.order);
+    if (o.stencil != 0 && o.stencil != 7 && o.stencil != 19) return fail(GPE_ERR_ARG, "stencil must be 7 or 19");
     if (o.sched != GPE_SCHED_WAVE && o.sched != GPE_SCHED_WAVE2 && o.sched != GPE_SCHED_STAGED)
         return fail(GPE_ERR_ARG, "unknown schedule %d", o.sched);
     if (o.chunk < 0 || o.chunk > 4096) return fail(GPE_ERR_ARG, "chunk must be in [0, 4096]");
@@ -492,6 +524,7 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
     g->mask_mode = o.mask_mode;
     g->order = o.order;
     g->sched = o.sched;
+    g->stencil = o.stencil == 19 ? 19 : 7;
     // bricks per wavefront task: about 2048 lattice cells for block tasks,
     // about 1024 for the warp tasks of WAVE2
     g->cb = o.chunk > 0 ? o.chunk : std::max(1, (o.sched == GPE_SCHED_WAVE2 ? 1024 : 2048) / g->bc);
@@ -646,6 +679,23 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
         BUILD_TRY(dev_alloc_t(&g->d_rec7, total * 7));
         BUILD_CUDA(cudaMemcpyAsync(g->d_rec7, h7.data(), h7.size() * sizeof(BrickRec), cudaMemcpyHostToDevice, st));
         BUILD_CUDA(cudaStreamSynchronize(st));
+        if (g->stencil == 19) {
+            int32_t *d_e = nullptr;
+            BUILD_TRY(dev_alloc_t(&d_e, total * 12));
+            k_edge_neighbors<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, coords, g->nbx, g->nby, g->nbz,
+                                                                            g->d_bvol, d_e);
+            std::vector<int32_t> he(total * 12);
+            cudaError_t e1 = cudaGetLastError();
+            if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(he.data(), d_e, he.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+            if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+            dev_free(d_e);
+            BUILD_CUDA(e1);
+            std::vector<BrickRec> h19;
+            build_rec19(hrec, hnbr, he, h19);
+            BUILD_TRY(dev_alloc_t(&g->d_rec19, total * 19));
+            BUILD_CUDA(cudaMemcpyAsync(g->d_rec19, h19.data(), h19.size() * sizeof(BrickRec), cudaMemcpyHostToDevice, st));
+            BUILD_CUDA(cudaStreamSynchronize(st));
+        }
     }
     for (int sl = 0; sl < g->n_slots; ++sl) {
         BUILD_TRY(dev_alloc_t(&g->d_V[sl], g->n_packed));

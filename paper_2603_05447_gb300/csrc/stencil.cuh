@@ -37,6 +37,8 @@ struct KernelCfg {
 #define GPE_MINB_D 3
 #endif
 #define GPE_BOUNDS(R) __launch_bounds__(KernelCfg<R>::THREADS, (min_blocks<R, BX, BY, BZ>()))
+// kernels templated on the stencil NP: the 19-point form needs more registers
+#define GPE_BOUNDS_NP(R) __launch_bounds__(KernelCfg<R>::THREADS, (NP == 19 ? 2 : min_blocks<R, BX, BY, BZ>()))
 
 // ------------------------------------------------------------ packed layout
 // supported brick shapes (shape id, BX, BY, BZ)
@@ -48,11 +50,12 @@ struct KernelCfg {
 struct GridView {
     const int32_t *nbr;
     const BrickRec *rec;
-    const BrickRec *rec7;  // per brick: its record, then its six face neighbours' (empty if absent)
+    const BrickRec *rec7;   // per brick: its record, then its six face neighbours' (empty if absent)
     int64_t nb;
+    const BrickRec *rec19;  // 19-point grids: the record, 6 face and 12 edge neighbours' records
 };
 
-inline GridView view(const gpe_grid *g) { return GridView{g->d_nbr, g->d_rec, g->d_rec7, g->nb}; }
+inline GridView view(const gpe_grid *g) { return GridView{g->d_nbr, g->d_rec, g->d_rec7, g->nb, g->d_rec19}; }
 
 // segment geometry of a brick shape (BX must be 8: two segments per row)
 template <int BX, int BY, int BZ>
@@ -147,6 +150,32 @@ __device__ __forceinline__ bool finite_v(const CT &v)
         return isfinite(v.x) && isfinite(v.y);
     else
         return isfinite(v);
+}
+template <typename CT>
+__device__ __forceinline__ CT vadd(const CT &a, const CT &b)
+{
+    if constexpr (is_cplx<CT>()) {
+        CT o;
+        o.x = a.x + b.x;
+        o.y = a.y + b.y;
+        return o;
+    } else {
+        return a + b;
+    }
+}
+// w (e - 2 f + 4 c): one mixed second difference of App. B's 19-point
+// stencil from its edge sum e, face sum f and centre c
+template <typename CT, typename R>
+__device__ __forceinline__ CT mixv(const CT &e, const CT &f, const CT &c, R w)
+{
+    if constexpr (is_cplx<CT>()) {
+        CT o;
+        o.x = w * (e.x - (R)2 * f.x + (R)4 * c.x);
+        o.y = w * (e.y - (R)2 * f.y + (R)4 * c.y);
+        return o;
+    } else {
+        return w * (e - (R)2 * f + (R)4 * c);
+    }
 }
 // one component of the 7-point Laplacian (Eq. (B1)) from opposite-neighbour
 // sums: (x- + x+)/hx^2 + (y- + y+)/hy^2 + (z- + z+)/hz^2 - c6 c
@@ -313,9 +342,14 @@ __device__ __forceinline__ CT ld1(const CT *p)
 // of the brick and its six face neighbours and the brick's stored segments in
 // order, each as its tile slot and x-halo row (slot | h << 8).  The records of the warp's next brick are fetched into nrec while
 // the current brick is processed.
-template <typename CT, int BX, int BY, int BZ>
+template <typename CT, int BX, int BY, int BZ, int NP = 7>
 struct WarpSpace {
     static constexpr int SX = BX / 4, TY = BY + 2, TZ = BZ + 2;
+    // records: own and 6 face neighbours (7-point), and 12 edge neighbours
+    // (19-point); x-halo columns: rows y in [0, BY) x z in [0, BZ), or with
+    // the halo rows y = -1, BY and planes z = -1, BZ for the 19-point stencil
+    static constexpr int NR = NP == 19 ? 19 : 7;
+    static constexpr int XH = NP == 19 ? TY * TZ : BY * BZ;
     static constexpr int NSLOT = SX * TY * TZ;                   // segment slots incl. y/z halos
     static constexpr int UPS = (int)(4 * sizeof(CT) / 16);       // 16-byte units per segment
     // plane stride (in units) = 4 (UPS 2) or 2 (UPS 4) mod 8: the UPS units of
@@ -326,13 +360,13 @@ struct WarpSpace {
     static constexpr int NSEG = Seg<BX, BY, BZ>::NSEG;
     static constexpr int ROW = SX, PLANE = SX * TY;              // slot strides in y and z
     __device__ __forceinline__ static int slot(int hx, int y, int z) { return hx + SX * ((y + 1) + TY * (z + 1)); }
-    __device__ __forceinline__ static int h(int y, int z) { return y + BY * z; }
+    __device__ __forceinline__ static int h(int y, int z) { return NP == 19 ? (y + 1) + TY * (z + 1) : y + BY * z; }
     uint4 units[UPS][PSTR];
-    CT xlo[BY * BZ];  // x = -1
-    CT xhi[BY * BZ];  // x = BX
-    BrickRec rec[7];
+    CT xlo[XH];  // x = -1
+    CT xhi[XH];  // x = BX
+    alignas(16) BrickRec rec[NR];
 #if GPE_REC_AHEAD
-    BrickRec nrec[7];  // records of the warp's next brick, fetched ahead
+    BrickRec nrec[NR];  // records of the warp's next brick, fetched ahead
     long long nrec_b;  // brick whose records nrec holds (-1: none)
     uint16_t list[NSEG];
     uint8_t pad[(16 - ((2 * NSEG + 8) % 16)) % 16];
@@ -372,10 +406,10 @@ struct WarpSpace {
     }
 };
 
-template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T, int NP = 7>
 constexpr size_t smem_bytes()
 {
-    return (size_t)KernelCfg<R>::NW * sizeof(WarpSpace<CT, BX, BY, BZ>);
+    return (size_t)KernelCfg<R>::NW * sizeof(WarpSpace<CT, BX, BY, BZ, NP>);
 }
 
 // the calling warp's workspace (call once per kernel: it resets the
@@ -388,11 +422,11 @@ constexpr int min_blocks()
     return fit < 1 ? 1 : (fit < cap ? fit : cap);
 }
 
-template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T>
-__device__ __forceinline__ WarpSpace<CT, BX, BY, BZ> &warp_space()
+template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T, int NP = 7>
+__device__ __forceinline__ WarpSpace<CT, BX, BY, BZ, NP> &warp_space()
 {
     extern __shared__ __align__(16) unsigned char gpe_smem[];
-    auto &ws = reinterpret_cast<WarpSpace<CT, BX, BY, BZ> *>(gpe_smem)[threadIdx.x >> 5];
+    auto &ws = reinterpret_cast<WarpSpace<CT, BX, BY, BZ, NP> *>(gpe_smem)[threadIdx.x >> 5];
 #if GPE_REC_AHEAD
     if ((threadIdx.x & 31) == 0) ws.nrec_b = -1;
     __syncwarp();
@@ -421,32 +455,33 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Records of brick b (slot 0) and of its six face neighbours (slots 1..6,
-// order -x +x -y +y -z +z; an absent neighbour has an empty record) into
-// ws.rec, one 224-byte row of rec7 moved by 14 lanes: from ws.nrec when it
-// was fetched ahead, else from global memory.  Then the row of brick `next`
-// (if >= 0) is fetched ahead into ws.nrec by cp.async; it completes with the
-// tile's copies.
+// Records of brick b (slot 0), of its six face neighbours (slots 1..6,
+// order -x +x -y +y -z +z) and, for the 19-point stencil, of its 12 edge
+// neighbours (slots 7..18: xy, xz, yz edges; order as in the grid builder);
+// an absent neighbour has an empty record.  One row (224 or 608 bytes) moved
+// into ws.rec: from ws.nrec when it was fetched ahead, else from global
+// memory.  Then the row of brick `next` (if >= 0) is fetched ahead into
+// ws.nrec by cp.async; it completes with the tile's copies.
 template <typename WS>
 __device__ __forceinline__ void fetch_recs(WS &ws, const GridView &G, int64_t b, int64_t next)
 {
+    constexpr int NU = 2 * WS::NR;  // 16-byte words of one row of records
+    const uint4 *rows = reinterpret_cast<const uint4 *>(WS::NR == 19 ? G.rec19 : G.rec7);
     const int lane = threadIdx.x & 31;
     cp_async_wait_all();
     __syncwarp();
 #if GPE_REC_AHEAD
     const bool ahead = ws.nrec_b == (long long)b;
-    if (lane < 14)
-        reinterpret_cast<uint4 *>(ws.rec)[lane] = ahead ? reinterpret_cast<const uint4 *>(ws.nrec)[lane]
-                                                        : __ldg(reinterpret_cast<const uint4 *>(G.rec7 + 7 * b) + lane);
+    for (int u = lane; u < NU; u += 32)
+        reinterpret_cast<uint4 *>(ws.rec)[u] = ahead ? reinterpret_cast<const uint4 *>(ws.nrec)[u] : __ldg(rows + NU * b + u);
     __syncwarp();
-    if (next >= 0 && lane < 14)
-        cp_async16(reinterpret_cast<uint4 *>(ws.nrec) + lane, reinterpret_cast<const uint4 *>(G.rec7 + 7 * next) + lane,
-                   true);
+    if (next >= 0)
+        for (int u = lane; u < NU; u += 32) cp_async16(reinterpret_cast<uint4 *>(ws.nrec) + u, rows + NU * next + u, true);
     if (lane == 0) ws.nrec_b = next;
     __syncwarp();
 #else
     (void)next;
-    if (lane < 14) reinterpret_cast<uint4 *>(ws.rec)[lane] = __ldg(reinterpret_cast<const uint4 *>(G.rec7 + 7 * b) + lane);
+    for (int u = lane; u < NU; u += 32) reinterpret_cast<uint4 *>(ws.rec)[u] = __ldg(rows + NU * b + u);
     __syncwarp();
 #endif
 }
@@ -476,12 +511,13 @@ struct NoPre {
 // stores coalesce.  The first 32 segments' operands are loaded while the tile
 // is in flight, the next 32's while a group is computed.  With xf the identity the tile is filled by cp.async;
 // otherwise through registers, where xf is applied.
-template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename LOAD, typename BODY>
-__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b, int64_t next,
-                                            const CT *src, XF xf, R ihx2, R ihy2, R ihz2, LOAD load, BODY body)
+template <int BX, int BY, int BZ, bool CG, typename CT, int NP, typename R, typename XF, typename LOAD, typename BODY>
+__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, const GridView &G, int64_t b,
+                                            int64_t next, const CT *src, XF xf, R ihx2, R ihy2, R ihz2, LOAD load,
+                                            BODY body)
 {
     using S = Seg<BX, BY, BZ>;
-    using W = WarpSpace<CT, BX, BY, BZ>;
+    using W = WarpSpace<CT, BX, BY, BZ, NP>;
     constexpr bool ASYNC = std::is_same<XF, Identity>::value;
     const int lane = threadIdx.x & 31;
     fetch_recs(ws, G, b, next);
@@ -561,18 +597,44 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
     // operands of the first 32 stored segments, while the tile is in flight
     typename std::decay<decltype(load(0u))>::type p0{};
     if (lane < nst) p0 = load(R0.off + 4u * (uint32_t)lane);
-    // -x / +x faces: single cells (x = BX-1 of the -x brick, x = 0 of the +x brick)
-    for (int u = lane; u < 2 * BY * BZ; u += 32) {
-        const int face = u / (BY * BZ), v_ = u % (BY * BZ);
-        const int y = v_ % BY, z = v_ / BY;
-        const int q = (face == 0 ? S::SX - 1 : 0) + S::SX * y + S::PLANE * z;
-        uint32_t j;
-        CT v = czero<CT>();
-        if (seg_index(ws.rec[1 + face], q, j)) {
-            j += face == 0 ? 3 : 0;
-            v = xf(ld1<CG>(src + j), j);
+    if constexpr (NP == 19) {
+        // y/z edge rows (y = -1 or BY, z = -1 or BZ) from the four yz-edge
+        // neighbours (records 15..18: (0,-1,-1) (0,+1,-1) (0,-1,+1) (0,+1,+1))
+#pragma unroll
+        for (int t = lane; t < 4 * S::SX * LPS; t += 32) {
+            const int v = t / LPS, e = v / S::SX, hx = v % S::SX;
+            const int ys = (e & 1) ? 0 : BY - 1, zs = (e & 2) ? 0 : BZ - 1;
+            seg_to(ws.rec[15 + e], hx + S::SX * ys + S::PLANE * zs,
+                   W::slot(hx, (e & 1) ? BY : -1, (e & 2) ? BZ : -1), t % LPS);
         }
-        (face == 0 ? ws.xlo : ws.xhi)[W::h(y, z)] = v;
+    }
+    // -x / +x faces: single cells (x = BX-1 of the -x brick, x = 0 of the +x
+    // brick); for the 19-point stencil also on the halo rows and planes,
+    // from the xy-edge (records 7..10) and xz-edge (11..14) neighbours
+    {
+        constexpr int HY = NP == 19 ? BY + 2 : BY, HZ = NP == 19 ? BZ + 2 : BZ, O = NP == 19 ? 1 : 0;
+        for (int u = lane; u < 2 * HY * HZ; u += 32) {
+            const int face = u / (HY * HZ), v_ = u % (HY * HZ);
+            const int y = v_ % HY - O, z = v_ / HY - O;
+            const bool yin = y >= 0 && y < BY, zin = z >= 0 && z < BZ;
+            CT v = czero<CT>();
+            if (yin || zin) {  // the y-z corners are read by no stencil
+                int r = 1 + face, ys = y, zs = z;
+                if (!yin) {
+                    r = 7 + face + (y == BY ? 2 : 0);
+                    ys = y < 0 ? BY - 1 : 0;
+                } else if (!zin) {
+                    r = 11 + face + (z == BZ ? 2 : 0);
+                    zs = z < 0 ? BZ - 1 : 0;
+                }
+                uint32_t j;
+                if (seg_index(ws.rec[r], (face == 0 ? S::SX - 1 : 0) + S::SX * ys + S::PLANE * zs, j)) {
+                    j += face == 0 ? 3 : 0;
+                    v = xf(ld1<CG>(src + j), j);
+                }
+            }
+            (face == 0 ? ws.xlo : ws.xhi)[W::h(y, z)] = v;
+        }
     }
     cp_async_wait_all();
     __syncwarp();
@@ -597,6 +659,43 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
             const CT rr = i == 3 ? xp : c[i + 1];
             L[i] = lapv(rr, l, yp[i], ym[i], zp[i], zm[i], c[i], ihx2, ihy2, ihz2, c6);
         }
+        if constexpr (NP == 19) {
+            // App. B: + w_ab (edges_ab - 2 faces_ab + 4 c) per plane ab, with
+            // w_ab = (h_a^2 + h_b^2) / (12 h_a^2 h_b^2) = (1/h_a^2 + 1/h_b^2) / 12
+            const R wxy = (ihx2 + ihy2) / (R)12, wxz = (ihx2 + ihz2) / (R)12, wyz = (ihy2 + ihz2) / (R)12;
+            const int row = sl / S::SX, y = row % W::TY - 1, z = row / W::TY - 1;
+            auto left = [&](int s2, int yy, int zz) { return hx == 0 ? ws.xlo[W::h(yy, zz)] : ws.last(s2 - 1); };
+            auto right = [&](int s2, int yy, int zz) {
+                return hx == S::SX - 1 ? ws.xhi[W::h(yy, zz)] : ws.first(s2 + 1);
+            };
+            const CT yml = left(sl - W::ROW, y - 1, z), ymr = right(sl - W::ROW, y - 1, z);
+            const CT ypl = left(sl + W::ROW, y + 1, z), ypr = right(sl + W::ROW, y + 1, z);
+            const CT zml = left(sl - W::PLANE, y, z - 1), zmr = right(sl - W::PLANE, y, z - 1);
+            const CT zpl = left(sl + W::PLANE, y, z + 1), zpr = right(sl + W::PLANE, y, z + 1);
+            CT eyz[4], t4[4];
+            ws.get(sl - W::ROW - W::PLANE, eyz);
+            ws.get(sl + W::ROW - W::PLANE, t4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) eyz[i] = vadd(eyz[i], t4[i]);
+            ws.get(sl - W::ROW + W::PLANE, t4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) eyz[i] = vadd(eyz[i], t4[i]);
+            ws.get(sl + W::ROW + W::PLANE, t4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                eyz[i] = vadd(eyz[i], t4[i]);
+                const CT l = i == 0 ? xm : c[i - 1];
+                const CT rr = i == 3 ? xp : c[i + 1];
+                const CT exy = vadd(vadd(i == 0 ? yml : ym[i - 1], i == 3 ? ymr : ym[i + 1]),
+                                    vadd(i == 0 ? ypl : yp[i - 1], i == 3 ? ypr : yp[i + 1]));
+                const CT exz = vadd(vadd(i == 0 ? zml : zm[i - 1], i == 3 ? zmr : zm[i + 1]),
+                                    vadd(i == 0 ? zpl : zp[i - 1], i == 3 ? zpr : zp[i + 1]));
+                const CT lr = vadd(l, rr);
+                L[i] = vadd(L[i], mixv(exy, vadd(lr, vadd(ym[i], yp[i])), c[i], wxy));
+                L[i] = vadd(L[i], mixv(exz, vadd(lr, vadd(zm[i], zp[i])), c[i], wxz));
+                L[i] = vadd(L[i], mixv(eyz[i], vadd(vadd(ym[i], yp[i]), vadd(zm[i], zp[i])), c[i], wyz));
+            }
+        }
         body(R0.off + 4u * (uint32_t)r, pre, c, L);
     };
     // each iteration loads the operands of the next before computing its own
@@ -610,9 +709,9 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const
 }
 
 // the same without prefetched operands: body(idx, c, L)
-template <int BX, int BY, int BZ, bool CG, typename CT, typename R, typename XF, typename BODY>
-__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ> &ws, const GridView &G, int64_t b, int64_t next,
-                                            const CT *src, XF xf, R ihx2, R ihy2, R ihz2, BODY body)
+template <int BX, int BY, int BZ, bool CG, typename CT, int NP, typename R, typename XF, typename BODY>
+__device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, const GridView &G, int64_t b,
+                                            int64_t next, const CT *src, XF xf, R ihx2, R ihy2, R ihz2, BODY body)
 {
     brick_apply<BX, BY, BZ, CG>(ws, G, b, next, src, xf, ihx2, ihy2, ihz2, NoPre(),
                                 [&](uint32_t idx, const NoPre::P &, const CT(&c)[4], const CT(&L)[4]) {
@@ -815,9 +914,9 @@ struct Rk4Body {
 };
 
 // One RK4 stage on brick b, one warp, lane = segment within each group of 32.
-template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG, int st>
+template <typename R, int BX, int BY, int BZ, bool BLEND, bool CG, int st, int NP = 7>
 __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G, int64_t b, int64_t next,
-                                          WarpSpace<typename Cx<R>::T, BX, BY, BZ> &ws, R s)
+                                          WarpSpace<typename Cx<R>::T, BX, BY, BZ, NP> &ws, R s)
 {
     using B = Rk4Body<R, BLEND, CG, st>;
     const B body(a, s);
@@ -825,33 +924,33 @@ __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G,
                                 [&](uint32_t idx) { return body.load(idx); }, body);
 }
 
-template <typename R, int BX, int BY, int BZ, bool BLEND, int ST>
-__global__ void GPE_BOUNDS(R) k_rk4_staged(const RkArgs<R> a, const GridView G)
+template <typename R, int BX, int BY, int BZ, bool BLEND, int ST, int NP = 7>
+__global__ void GPE_BOUNDS_NP(R) k_rk4_staged(const RkArgs<R> a, const GridView G)
 {
     constexpr int NW = KernelCfg<R>::NW;
-    auto &ws = warp_space<R, BX, BY, BZ>();
+    auto &ws = warp_space<R, BX, BY, BZ, typename Cx<R>::T, NP>();
     const int warp = threadIdx.x >> 5;
     const R s = stage_s<R, BLEND>(a, ST);
     const int64_t stride = (int64_t)gridDim.x * NW;
     for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride)
-        rk4_brick<R, BX, BY, BZ, BLEND, false, ST>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, s);
+        rk4_brick<R, BX, BY, BZ, BLEND, false, ST, NP>(a, G, b, b + stride < G.nb ? b + stride : -1, ws, s);
 }
 
 // the four stage kernels of one shape, static (BLEND false) or blended, and
 // their launch shape
-template <typename R, int BX, int BY, int BZ>
+template <typename R, int BX, int BY, int BZ, int NP = 7>
 struct Rk4Stages {
     using K = void (*)(RkArgs<R>, GridView);
     static constexpr int NW = KernelCfg<R>::NW;
     static constexpr int THREADS = 32 * NW;
-    static constexpr size_t smem() { return smem_bytes<R, BX, BY, BZ>(); }
+    static constexpr size_t smem() { return smem_bytes<R, BX, BY, BZ, typename Cx<R>::T, NP>(); }
     static K get(bool blend, int st)
     {
         static const K t[2][4] = {
-            {k_rk4_staged<R, BX, BY, BZ, false, 0>, k_rk4_staged<R, BX, BY, BZ, false, 1>,
-             k_rk4_staged<R, BX, BY, BZ, false, 2>, k_rk4_staged<R, BX, BY, BZ, false, 3>},
-            {k_rk4_staged<R, BX, BY, BZ, true, 0>, k_rk4_staged<R, BX, BY, BZ, true, 1>,
-             k_rk4_staged<R, BX, BY, BZ, true, 2>, k_rk4_staged<R, BX, BY, BZ, true, 3>}};
+            {k_rk4_staged<R, BX, BY, BZ, false, 0, NP>, k_rk4_staged<R, BX, BY, BZ, false, 1, NP>,
+             k_rk4_staged<R, BX, BY, BZ, false, 2, NP>, k_rk4_staged<R, BX, BY, BZ, false, 3, NP>},
+            {k_rk4_staged<R, BX, BY, BZ, true, 0, NP>, k_rk4_staged<R, BX, BY, BZ, true, 1, NP>,
+             k_rk4_staged<R, BX, BY, BZ, true, 2, NP>, k_rk4_staged<R, BX, BY, BZ, true, 3, NP>}};
         return t[blend ? 1 : 0][st];
     }
 };

@@ -55,7 +55,7 @@ class gpe_box(C.Structure):
 class gpe_grid_opts(C.Structure):
     _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32),
                 ("mask_mode", C.c_int32), ("order", C.c_int32), ("sched", C.c_int32),
-                ("chunk", C.c_int32), ("reserved", C.c_int32)]
+                ("chunk", C.c_int32), ("stencil", C.c_int32)]
 
 
 class gpe_potential(C.Structure):
@@ -246,13 +246,14 @@ def make_box(nx, ny, nz, hx, hy=None, hz=None, x0=None, y0=None, z0=None) -> gpe
 
 
 def make_opts(brick=(8, 8, 8), mask_mode=GPE_MASK_CELL, order=GPE_ORDER_ZMAJOR, sched=GPE_SCHED_STAGED,
-              chunk=0) -> gpe_grid_opts:
+              chunk=0, stencil=7) -> gpe_grid_opts:
     o = gpe_grid_opts()
     o.bx, o.by, o.bz = brick
     o.mask_mode = mask_mode
     o.order = order
     o.sched = sched
     o.chunk = chunk
+    o.stencil = stencil
     return o
 
 

@@ -72,3 +72,34 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gpe.gpe_real_params) == 2 * 8 + 4 * 4 + 8 + 16 * 8
     assert ctypes.sizeof(gpe.gpe_obs) == 7 * 8
     assert ctypes.sizeof(gpe.gpe_grid_info) == 4 * 8 + 6 * 4 + 8 + ctypes.sizeof(gpe.gpe_box)
+
+
+def header_structs():
+    """Field names, in order, of every `typedef struct name {...} name;` in
+    include/*.h (arrays keep their name)."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"typedef\s+struct\s+(\w+)\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+            names = []
+            for decl in m.group(2).split(";"):
+                decl = decl.strip()
+                if not decl:
+                    continue
+                body = decl.split(None, 1)[1]          # drop the type
+                for part in body.split(","):
+                    names.append(re.sub(r"\[.*?\]", "", part).strip())
+            out[m.group(3)] = names
+    return out
+
+
+def test_binding_structs_match_the_header_field_by_field():
+    """A renamed or reordered field in the binding would silently drop a
+    setting (ctypes accepts unknown attributes): compare names and order."""
+    structs = header_structs()
+    assert "gpe_grid_opts" in structs and "gpe_real_params" in structs
+    for name, fields in structs.items():
+        cls = getattr(gpe, name, None)
+        if cls is None:
+            continue
+        assert [f[0] for f in cls._fields_] == fields, name
