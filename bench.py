@@ -335,6 +335,31 @@ def _run_ours(args, torch, world, rank, local):
             integ[name] = {"value": n_active / (ms / 1e3), "unit": "cell-steps/s", "ms_per_step": ms,
                            "stages": 3 if name == "RKHE3" else 6}
 
+    # ---- the 19-point stencil of App. B on the same shell (its own grid)
+    st19 = None
+    if not args.quick or args.integrators:
+        b_ = wl.box
+        g19 = gpe.gpe_grid_create_analytic(gpe.make_box(b_.nx, b_.ny, b_.nz, b_.hx),
+                                           gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes),
+                                           wl.V_cut, gpe.make_opts(tuple(args.brick), stencil=19))
+        s19 = gpe.gpe_state_create(g19, gpe.GPE_C64)
+        gpe.gpe_state_load(s19, psi64, gpe.GPE_LAYOUT_COMPACT)
+        for _ in range(max(1, args.warmup)):
+            gpe.gpe_step_real(s19, params, STEPS_PER_BENCH // 10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(torch.cuda.current_stream())
+        gpe.gpe_step_real(s19, params, STEPS_PER_BENCH)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms19 = e0.elapsed_time(e1) / STEPS_PER_BENCH
+        gpe.gpe_state_load(s19, psi64, gpe.GPE_LAYOUT_COMPACT)
+        itp19 = time_itp(gpe, torch, s19, gpe.gpe_imag_params(wl.g, dt, wl.N), 1, 1)
+        st19 = {"value": n_active / (ms19 / 1e3), "unit": "cell-steps/s", "ms_per_rk4_step": ms19,
+                "ms_per_itp_step": itp19}
+        gpe.gpe_state_destroy(s19)
+        gpe.gpe_grid_destroy(g19)
+
     # ---- imaginary-time steps on the same grid (complex64, FP64 norm)
     gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
     ip = gpe.gpe_imag_params(wl.g, dt, wl.N)
@@ -359,7 +384,7 @@ def _run_ours(args, torch, world, rank, local):
                               "grid_build_s": round(t_build, 4),
                               "ms_per_rk4_step": rk_ms, "achieved_gbs": achieved, "n_active": n_active,
                               "ms_per_itp_step": itp_ms, "ms_per_itp_step_real": itpr_ms,
-                              "integrators": integ or None,
+                              "integrators": integ or None, "stencil19": st19,
                               "gpu_launches": gpu_launches}), flush=True)
         return
 
@@ -433,6 +458,7 @@ def _run_ours(args, torch, world, rank, local):
                 "d2h_bytes_per_step": n_stored * 8 + 7 * 8},
         "itp": itp,
         "integrators": integ,
+        "stencil19": st19,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
