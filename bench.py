@@ -104,7 +104,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- workload
 WORKLOADS = {"shell1024": "SHELL_1024", "shell512": "SHELL_512"}
-EXTRA = ("ramp2048", "adjoint512", "batch", "roi_sweep")
+EXTRA = ("ramp2048", "adjoint512", "batch", "roi_sweep", "stages512")
 _workload_name = "shell1024"
 
 
@@ -524,6 +524,69 @@ def _core_state(gpe, inputs, rw, grid, dtype):
     return np.ascontiguousarray(out.astype(np.complex64 if dtype == gpe.GPE_C64 else np.complex128))
 
 
+def stages_run(gpe, inputs, torch, n_stages=66, steps_per_stage=20):
+    """Multi-stage ramp (Sec. V) on a 512^3 shell: 67 dense FP32 potentials
+    on the device, evenly spaced blends of the shell and a softer, slightly
+    rounder shell (inputs.stage_fractions); every stage selects its region
+    again at 5 max(mu_i, mu_{i+1}) and remaps the state.  Timed twice: with
+    `steps_per_stage` RK4 steps a stage, and with one, whose difference gives
+    the step rate; the report gives each stage's regrid time."""
+    wl = inputs.SHELL_512
+    b = wl.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    a, bb, c = wl.axes
+    end = inputs.EllipsoidShell(0.6 * wl.w, a, bb + 0.01, c + 0.02)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # endpoint potentials, evaluated on the host in z-slabs, FP64 on the device
+    V0 = torch.empty((b.nz, b.ny, b.nx), dtype=torch.float64, device=dev)
+    V1 = torch.empty_like(V0)
+    x, y, z = b.axes()
+    for k0 in range(0, b.nz, 32):
+        Z, Y, X = np.meshgrid(z[k0:k0 + 32], y, x, indexing="ij")
+        V0[k0:k0 + 32].copy_(torch.from_numpy(wl.potential(X, Y, Z)))
+        V1[k0:k0 + 32].copy_(torch.from_numpy(end(X, Y, Z)))
+    pots = [((1.0 - s) * V0 + s * V1).to(torch.float32) for s in inputs.stage_fractions(n_stages)]
+    del V0, V1
+    mu0 = gpe.gpe_tf_mu_dense(gb, pots[0], wl.g, wl.N)
+    g0 = gpe.gpe_grid_create_dense(gb, pots[0], 5.0 * mu0, gpe.make_opts((8, 8, 4)))
+    info0 = gpe.gpe_grid_get_info(g0)
+    dt = 0.2 / (6.0 / wl.h ** 2 + 2.0 * info0.v_max)     # the softer shells only lower |V|
+    s0 = gpe.gpe_state_create(g0, gpe.GPE_C64)
+    idx, i, j, k = gpe.packed_coords(g0)
+    psi = np.zeros(info0.n_packed, np.complex128)
+    psi[idx] = np.sqrt(np.maximum(mu0 - wl.potential(b.x0 + i * b.hx, b.y0 + j * b.hy, b.z0 + k * b.hz), 0.0)
+                       / wl.g)
+    psi *= math.sqrt(wl.N / (np.sum(np.abs(psi) ** 2) * b.dV))
+    gpe.gpe_state_load(s0, np.ascontiguousarray(psi.astype(np.complex64)), gpe.GPE_LAYOUT_COMPACT)
+    params = gpe.stage_params(wl.g, wl.N, dt, 5.0)
+    runs = {}
+    for n in (1, steps_per_stage, steps_per_stage):      # the first run warms up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grid, st, rep = gpe.gpe_ramp_stages(s0, pots, [n * dt] * n_stages, params)
+        el = time.perf_counter() - t0
+        gpe.gpe_state_destroy(st)
+        gpe.gpe_grid_destroy(grid)
+        runs[n] = (el, rep)
+    gpe.gpe_state_destroy(s0)
+    gpe.gpe_grid_destroy(g0)
+    (t1, rep1), (tn, rep) = runs[1], runs[steps_per_stage]
+    cell_steps = sum(r["n_active"] * r["steps"] for r in rep)
+    step_s = (tn - t1) / (steps_per_stage - 1) / n_stages        # one step of an average stage
+    regrid_s = sum(r["regrid_s"] for r in rep)
+    return dict(metric="multi-stage ramp: active-cell RK4 steps/s including every regrid (complex64)",
+                unit="cell-steps/s", value=cell_steps / tn, seconds=tn, stages=n_stages,
+                steps_per_stage=steps_per_stage, dt=dt,
+                step_cell_steps_per_s=sum(r["n_active"] for r in rep) / n_stages / step_s,
+                regrid_ms_per_stage=regrid_s / n_stages * 1e3,
+                other_ms_per_stage=(tn - regrid_s - n_stages * steps_per_stage * step_s) / n_stages * 1e3,
+                n_active_first=rep[0]["n_active"], n_active_last=rep[-1]["n_active"],
+                norm_kept_min=min(r["norm_kept"] for r in rep), norm_end=rep[-1]["norm_end"],
+                config="512^3 box, shell semi-axes 240/216/192 cells, g=2000; 67 dense FP32 potentials blending "
+                       "it into a shell of 0.6x the stiffness and semi-axes +0.01/+0.02; region "
+                       "5 max(mu_i, mu_i+1) per stage")
+
+
 def roi_sweep(gpe, inputs, torch):
     """Boundary error of the region of interest (the study of Sec. IV,
     Fig. 2c, on a synthetic shell): ground states on regions V < r mu_TF in
@@ -591,6 +654,8 @@ def run_extra(args):
     with torch.cuda.stream(side):
         if args.workload == "roi_sweep":
             line.update(roi_sweep(gpe, inputs, torch))
+        elif args.workload == "stages512":
+            line.update(stages_run(gpe, inputs, torch))
         elif args.workload in ("ramp2048", "adjoint512"):
             rw = inputs.RAMP_2048 if args.workload == "ramp2048" else inputs.RAMP_512
             grid = _ramp_grid(gpe, rw)

@@ -166,6 +166,16 @@ int gpe_grid_create_blend(const gpe_box *box, const gpe_potential *pot0,
                           const gpe_grid_opts *opts, gpe_grid **out,
                           gpe_stream stream);
 
+/* The same union region for two dense potentials V0, V1 (nx*ny*nz values
+ * each, both of type V_dtype and both on the host or both on the device, as
+ * in gpe_grid_create_dense): active cells are those with V0 < cut0 or
+ * V1 < cut1; slot 0 holds V0 and slot 1 holds V1.  Synchronous. */
+int gpe_grid_create_blend_dense(const gpe_box *box, const void *V0,
+                                const void *V1, int V_dtype, int V_on_device,
+                                double cut0, double cut1,
+                                const gpe_grid_opts *opts, gpe_grid **out,
+                                gpe_stream stream);
+
 /* Replace potential slot 0 or 1 with a dense potential (same layout as
  * gpe_grid_create_dense); the region of interest is unchanged.  Synchronous. */
 int gpe_grid_set_potential(gpe_grid *grid, int slot, const void *V,
@@ -392,6 +402,71 @@ int gpe_batch_ground_state(gpe_batch *batch, const gpe_imag_params *per_shell,
                            int64_t *steps, gpe_obs *obs, gpe_stream stream);
 
 int gpe_batch_destroy(gpe_batch *batch);
+
+/* ------------------------------------------------------------------ stages */
+/* Multi-stage potential ramp (Sec. V).  The potential passes through the
+ * precomputed potentials pots[0], ..., pots[n_pots-1]; stage i (i = 0 ..
+ * n_pots-2) lasts durations[i] and interpolates linearly in time from
+ * pots[i] to pots[i+1].  At the start of every stage the region of interest
+ * is selected again and the wavefunction remapped onto it:
+ *   mu_i   = Thomas-Fermi chemical potential of pots[i] for g and N (as
+ *            gpe_tf_mu_*, Eq. (5)),
+ *   cut_i  = cut_factor * max(mu_i, mu_{i+1})   (cut_factor = 5 in Sec. V),
+ *   region = {V_i < cut_i} U {V_{i+1} < cut_i}, which holds every
+ *            intermediate potential's region {V(s) < cut_i} (the union of
+ *            the sublevel sets of a linear blend is that of its endpoints),
+ * then the stage runs n = ceil(durations[i] / dt) equal real-time steps of
+ * length durations[i] / n with V(t) = (1 - t/d) V_i + (t/d) V_{i+1}.  With
+ * t_hold > 0 a hold in pots[n_pots-1] follows on the region
+ * {V_last < cut_factor * mu_last}.
+ *
+ * psi0 is the initial state (complex, any grid over the box; it is read, not
+ * changed).  The stage grids use *opts, or psi0's grid options when opts is
+ * NULL.  A potential is analytic (analytic != NULL) or a dense box array
+ * (V, V_dtype, V_on_device as in gpe_grid_create_dense); all of them must be
+ * of one kind, and dense ones share V_dtype and V_on_device.
+ *
+ * On success *grid_out and *state_out receive the last stage's grid and the
+ * final state (owned by the caller: destroy the state, then the grid).
+ * report (may be NULL) receives n_pots - 1 entries, plus one for the hold.
+ * Each stage's grids exist only while the stage runs; two grids and two
+ * states are held at a time.  The remap drops the density outside the new
+ * region (norm_kept reports what is left); there is no renormalisation.
+ * Errors: GPE_ERR_ARG for bad arguments, else the failing call's code; on
+ * error nothing is returned and everything made so far is freed.
+ * Synchronous. */
+typedef struct gpe_ramp_pot {
+    const gpe_potential *analytic; /* non-NULL: analytic potential */
+    const void *V;                 /* else: dense nx*ny*nz array */
+    int32_t V_dtype, V_on_device;
+} gpe_ramp_pot;
+
+typedef struct gpe_stage_params {
+    double g, N;          /* interaction and atom number (Thomas-Fermi mu) */
+    double dt;            /* largest time step */
+    double cut_factor;    /* region cutoff over max(mu_i, mu_{i+1}) */
+    double t_hold;        /* hold in the last potential (0: none) */
+    int32_t integrator;   /* GPE_RK4, GPE_RKHE3, GPE_RKCK */
+    int32_t reserved;
+} gpe_stage_params;
+
+typedef struct gpe_stage_report {
+    double mu_a, mu_b;     /* Thomas-Fermi mu of the stage's two potentials */
+    double cut;            /* the cutoff used */
+    int64_t n_active;      /* active cells of the stage's grid */
+    int64_t steps;
+    double dt;             /* step length used */
+    double norm_kept;      /* sum |psi|^2 dV after the remap */
+    double norm_end;       /* at the end of the stage */
+    double regrid_s;       /* host seconds to build the grid, make the state
+                              and remap (waited for when report is given) */
+} gpe_stage_report;
+
+int gpe_ramp_stages(const gpe_state *psi0, const gpe_ramp_pot *pots,
+                    int n_pots, const double *durations,
+                    const gpe_stage_params *p, const gpe_grid_opts *opts,
+                    gpe_grid **grid_out, gpe_state **state_out,
+                    gpe_stage_report *report, gpe_stream stream);
 
 /* ------------------------------------------------------------------ adjoint */
 /* Ramp gradient by the discrete adjoint of the RK4 step (not in the paper:

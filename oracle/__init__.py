@@ -362,3 +362,54 @@ def ramp_loss_and_grad(grid: Grid, V0, V1, knots, T, g, dt, nsteps, psi0, psi_ta
         lam, gk = rk4_adjoint_step(grid, V0, V1, knots, T, g, t0 + s * dt, dt, states[s], lam)
         grad += gk
     return loss, grad, y
+
+
+def ramp_stages(Vs, h, durations, g, N, dt, psi0, cut_factor=5.0, t_hold=0.0, method="RK4"):
+    """Multi-stage ramp of Sec. V through the dense potentials Vs[0..M].
+
+    Stage i interpolates linearly in time from Vs[i] to Vs[i+1] over
+    durations[i].  Before it runs, the region of interest is selected again
+    with the cutoff cut_factor * max(mu_i, mu_{i+1}) (mu the Thomas-Fermi
+    chemical potential of Eq. (5) for g and N): every cell below the cutoff
+    in either endpoint potential.  The wavefunction is carried over on the
+    cells the two regions share (remapped between the old and new grids).
+    The stage takes ceil(d / dt) equal steps.  With t_hold > 0 a hold in the
+    last potential follows on {Vs[-1] < cut_factor * mu_M}.
+
+    psi0 is a dense box array (zero outside its own region).  Returns the
+    final dense psi and one record per stage (mu_a, mu_b, cut, n_active,
+    steps, dt, norm_kept, norm_end).
+    """
+    h = tuple(float(x) for x in (h if np.ndim(h) else (h, h, h)))
+    dV = h[0] * h[1] * h[2]
+    mu = [tf_mu(V, dV, g, N) for V in Vs]
+    psi = np.array(psi0, dtype=np.complex128)
+    M = len(Vs) - 1
+    records = []
+    for i in range(M + (1 if t_hold > 0 else 0)):
+        hold = i == M
+        if hold:
+            mu_a = mu_b = mu[M]
+            cut = cut_factor * mu_a
+            mask = Vs[M] < cut
+            d = t_hold
+        else:
+            mu_a, mu_b = mu[i], mu[i + 1]
+            cut = cut_factor * max(mu_a, mu_b)
+            mask = (Vs[i] < cut) | (Vs[i + 1] < cut)
+            d = durations[i]
+        grid = Grid(mask, h)
+        y = grid.compact(psi)          # cells outside the new region are dropped
+        norm_kept = float(np.sum(np.abs(y) ** 2) * dV)
+        n = max(1, int(np.ceil(d / dt * (1.0 - 1e-12))))
+        dts = d / n
+        if hold:
+            V0, V1, knots = grid.compact(Vs[M]), None, None
+        else:
+            V0, V1, knots = grid.compact(Vs[i]), grid.compact(Vs[i + 1]), np.array([0.0, 1.0])
+        for k in range(n):
+            y = rk_step(grid, V0, y, g, k * dts, dts, method, V1, knots, d)
+        psi = grid.dense(y)
+        records.append(dict(mu_a=mu_a, mu_b=mu_b, cut=cut, n_active=grid.n, steps=n, dt=dts,
+                            norm_kept=norm_kept, norm_end=float(np.sum(np.abs(y) ** 2) * dV)))
+    return psi, records

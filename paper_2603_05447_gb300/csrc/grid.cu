@@ -23,11 +23,11 @@ struct PotDesc {
     double p[8];
 };
 
-// V source for the builder: dense array, one analytic potential, or two
-// (ramp endpoints) whose union mask is taken.
+// V source for the builder: a dense array, one analytic potential, or two
+// potentials (ramp endpoints, analytic or dense) whose union mask is taken.
 struct VSource {
-    int mode;  // 0 dense, 1 analytic, 2 blend
-    const void *dense;
+    int mode;  // 0 dense, 1 analytic, 2 analytic blend, 3 dense blend
+    const void *dense, *dense1;
     int dtype;
     PotDesc p0, p1;
     double cut0, cut1;
@@ -55,12 +55,19 @@ __device__ __forceinline__ void cell_values(const VSource &src, const BoxD &bx, 
                                             int64_t j, int64_t k, double &v0, double &v1,
                                             bool &sel)
 {
-    if (src.mode == 0) {
+    if (src.mode == 0 || src.mode == 3) {
         int64_t lin = i + bx.nx * (j + bx.ny * k);
-        v0 = src.dtype == GPE_F64 ? ((const double *)src.dense)[lin]
-                                  : (double)((const float *)src.dense)[lin];
-        v1 = 0.0;
-        sel = v0 < src.cut0;
+        auto at = [&](const void *p) {
+            return src.dtype == GPE_F64 ? ((const double *)p)[lin] : (double)((const float *)p)[lin];
+        };
+        v0 = at(src.dense);
+        if (src.mode == 3) {
+            v1 = at(src.dense1);
+            sel = (v0 < src.cut0) || (v1 < src.cut1);
+        } else {
+            v1 = 0.0;
+            sel = v0 < src.cut0;
+        }
         return;
     }
     double x = bx.x0 + i * bx.hx, y = bx.y0 + j * bx.hy, z = bx.z0 + k * bx.hz;
@@ -121,7 +128,7 @@ __global__ void k_occupancy(VSource src, BoxD box, int BX, int BY, int BZ, int64
     if (q < nq) {
         const int64_t qx = q % nbx, qy = (q / nbx) % nby, qz = q / (nbx * nby);
         bool may = true;
-        if (src.mode != 0) {
+        if (src.mode == 1 || src.mode == 2) {
             const int64_t i0 = qx * BX, j0 = qy * BY, k0 = qz * BZ;
             const int64_t i1 = min(i0 + BX, box.nx) - 1, j1 = min(j0 + BY, box.ny) - 1, k1 = min(k0 + BZ, box.nz) - 1;
             const float xl = (float)(box.x0 + i0 * box.hx), xh = (float)(box.x0 + i1 * box.hx);
@@ -633,7 +640,7 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
 
     BUILD_TRY(dev_alloc_t(&g->d_mask, g->n_stored / 32));
     BUILD_TRY(dev_alloc_t(&tmpV[0], g->n_stored));
-    if (src.mode == 2) {
+    if (src.mode == 2 || src.mode == 3) {
         BUILD_TRY(dev_alloc_t(&tmpV[1], g->n_stored));
         g->n_slots = 2;
     }
@@ -802,6 +809,36 @@ extern "C" int gpe_grid_create_blend(const gpe_box *box, const gpe_potential *po
     src.cut0 = cut0;
     src.cut1 = cut1;
     return build_grid(box, src, opts, out, S(stream));
+}
+
+extern "C" int gpe_grid_create_blend_dense(const gpe_box *box, const void *V0, const void *V1, int V_dtype,
+                                           int V_on_device, double cut0, double cut1,
+                                           const gpe_grid_opts *opts, gpe_grid **out, gpe_stream stream)
+{
+    if (!out) return fail(GPE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    GPE_TRY(check_box(box));
+    cudaStream_t st = S(stream);
+    const void *d0 = nullptr, *d1 = nullptr;
+    void *own0 = nullptr, *own1 = nullptr;
+    GPE_TRY(stage_dense(box, V0, V_dtype, V_on_device, &d0, &own0, st));
+    int rc = stage_dense(box, V1, V_dtype, V_on_device, &d1, &own1, st);
+    if (rc == GPE_OK) {
+        VSource src{};
+        src.mode = 3;
+        src.dense = d0;
+        src.dense1 = d1;
+        src.dtype = V_dtype;
+        src.cut0 = cut0;
+        src.cut1 = cut1;
+        rc = build_grid(box, src, opts, out, st);
+    }
+    if (own0 || own1) {
+        cudaStreamSynchronize(st);
+        dev_free(own0);
+        dev_free(own1);
+    }
+    return rc;
 }
 
 extern "C" int gpe_grid_set_potential(gpe_grid *g, int slot, const void *V, int V_dtype, int V_on_device,

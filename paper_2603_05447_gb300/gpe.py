@@ -98,6 +98,25 @@ class gpe_tune_result(C.Structure):
 GPE_TUNE_REAL, GPE_TUNE_IMAG = 0, 1
 
 
+class gpe_ramp_pot(C.Structure):
+    _fields_ = [("analytic", C.POINTER(gpe_potential)), ("V", C.c_void_p), ("V_dtype", C.c_int32),
+                ("V_on_device", C.c_int32)]
+
+
+class gpe_stage_params(C.Structure):
+    _fields_ = [("g", C.c_double), ("N", C.c_double), ("dt", C.c_double), ("cut_factor", C.c_double),
+                ("t_hold", C.c_double), ("integrator", C.c_int32), ("reserved", C.c_int32)]
+
+
+class gpe_stage_report(C.Structure):
+    _fields_ = [("mu_a", C.c_double), ("mu_b", C.c_double), ("cut", C.c_double), ("n_active", C.c_int64),
+                ("steps", C.c_int64), ("dt", C.c_double), ("norm_kept", C.c_double), ("norm_end", C.c_double),
+                ("regrid_s", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GpeError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
@@ -118,6 +137,8 @@ _SIGS = {
     "gpe_grid_create_blend": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.c_double,
                                         C.POINTER(gpe_potential), C.c_double, C.POINTER(gpe_grid_opts),
                                         C.POINTER(_P), _P]),
+    "gpe_grid_create_blend_dense": (C.c_int, [C.POINTER(gpe_box), _P, _P, C.c_int, C.c_int, C.c_double,
+                                              C.c_double, C.POINTER(gpe_grid_opts), C.POINTER(_P), _P]),
     "gpe_grid_set_potential": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int, _P]),
     "gpe_grid_get_info": (C.c_int, [_P, C.POINTER(gpe_grid_info)]),
     "gpe_grid_bricks": (C.c_int, [_P, _P, _P]),
@@ -150,6 +171,9 @@ _SIGS = {
     "gpe_ramp_forward": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, C.c_int, C.POINTER(_P), _P]),
     "gpe_ramp_backward": (C.c_int, [_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P]),
     "gpe_tape_destroy": (C.c_int, [_P]),
+    "gpe_ramp_stages": (C.c_int, [_P, C.POINTER(gpe_ramp_pot), C.c_int, C.POINTER(C.c_double),
+                                  C.POINTER(gpe_stage_params), C.POINTER(gpe_grid_opts), C.POINTER(_P),
+                                  C.POINTER(_P), C.POINTER(gpe_stage_report), _P]),
     "gpe_overlap_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_double), _P]),
     "gpe_ground_state": (C.c_int, [_P, C.POINTER(gpe_imag_params), C.c_double, C.c_int64, C.c_int64,
                                    C.POINTER(C.c_int64), C.POINTER(gpe_obs), _P]),
@@ -340,6 +364,18 @@ def gpe_grid_create_blend(box, pot0, cut0, pot1, cut1, opts=None, stream=None):
     return out.value
 
 
+def gpe_grid_create_blend_dense(box, V0, V1, cut0, cut1, opts=None, stream=None):
+    p0, dev0 = pointer(V0)
+    p1, dev1 = pointer(V1)
+    if dev0 != dev1 or real_dtype_code(V0) != real_dtype_code(V1):
+        raise GpeError(GPE_ERR_ARG, "V0 and V1 must share dtype and location")
+    out = _P()
+    _check(load().gpe_grid_create_blend_dense(C.byref(box), p0, p1, real_dtype_code(V0), dev0, float(cut0),
+                                              float(cut1), C.byref(opts) if opts else None, C.byref(out),
+                                              stream_handle(stream)))
+    return out.value
+
+
 def gpe_grid_set_potential(grid, slot, V, stream=None):
     ptr, dev = pointer(V)
     _check(load().gpe_grid_set_potential(grid, int(slot), ptr, real_dtype_code(V), dev, stream_handle(stream)))
@@ -513,6 +549,36 @@ def gpe_ramp_backward(tape, target, n_knots, stream=None):
 
 def gpe_tape_destroy(tape):
     _check(load().gpe_tape_destroy(tape))
+
+
+def stage_params(g, N, dt, cut_factor=5.0, t_hold=0.0, integrator=GPE_RK4) -> gpe_stage_params:
+    p = gpe_stage_params()
+    p.g, p.N, p.dt, p.cut_factor, p.t_hold = float(g), float(N), float(dt), float(cut_factor), float(t_hold)
+    p.integrator = integrator
+    return p
+
+
+def gpe_ramp_stages(psi0, pots, durations, params, opts=None, stream=None):
+    """Multi-stage ramp (Sec. V) through ``pots`` (each a gpe_potential or a
+    dense float64/float32 array, all of one kind); returns (grid, state,
+    reports).  The caller destroys the state, then the grid."""
+    n = len(pots)
+    arr = (gpe_ramp_pot * n)()
+    keep = []
+    for i, P in enumerate(pots):
+        if isinstance(P, gpe_potential):
+            keep.append(P)
+            arr[i].analytic = C.pointer(P)
+        else:
+            ptr, dev = pointer(P)
+            arr[i].V, arr[i].V_dtype, arr[i].V_on_device = ptr, real_dtype_code(P), dev
+    dur = (C.c_double * max(n - 1, 1))(*[float(d) for d in durations])
+    reports = (gpe_stage_report * (n + 1))()
+    grid, state = _P(), _P()
+    _check(load().gpe_ramp_stages(psi0, arr, n, dur, C.byref(params), C.byref(opts) if opts else None,
+                                  C.byref(grid), C.byref(state), reports, stream_handle(stream)))
+    n_rep = n - 1 + (1 if params.t_hold > 0 else 0)
+    return grid.value, state.value, [reports[i].asdict() for i in range(n_rep)]
 
 
 def gpe_overlap_noalloc(a, b, n, dtype, dV, stream=None) -> complex:

@@ -274,6 +274,14 @@ RAMP_512 = RampWorkload(ShellWorkload(n=512, a_cells=200.0, g=5000.0), core_radi
 RAMP_48 = RampWorkload(ShellWorkload(n=48, a_cells=19.0, g=5000.0), core_radius=0.24)
 
 
+def stage_fractions(n_stages: int = 66) -> np.ndarray:
+    """Blend fractions s_k = k / n_stages of the stage potentials
+    V_k = (1 - s_k) V0 + s_k V1 of a multi-stage ramp between a ramp
+    workload's two endpoints: synthetic stand-ins for the precomputed
+    potentials of Sec. V (67 potentials, 66 stages)."""
+    return np.arange(n_stages + 1, dtype=np.float64) / n_stages
+
+
 def batch_shells(n: int = 64, seed: int = 4, scale_cells: float = 360.0):
     """Seeded batch of uneven ellipsoidal shells: radius r ~ U[0.5, 1] (semi-axis
     r * scale_cells cells), aspect ratios b/a, c/a ~ U[0.7, 1], thickness

@@ -86,9 +86,10 @@ def header_structs():
                 decl = decl.strip()
                 if not decl:
                     continue
-                body = decl.split(None, 1)[1]          # drop the type
-                for part in body.split(","):
-                    names.append(re.sub(r"\[.*?\]", "", part).strip())
+                # `type a, b[4]` or `const type *p`: each declarator's name is
+                # its last identifier once array bounds are dropped
+                for part in decl.split(","):
+                    names.append(re.findall(r"\w+", re.sub(r"\[.*?\]", "", part))[-1])
             out[m.group(3)] = names
     return out
 
@@ -97,9 +98,8 @@ def test_binding_structs_match_the_header_field_by_field():
     """A renamed or reordered field in the binding would silently drop a
     setting (ctypes accepts unknown attributes): compare names and order."""
     structs = header_structs()
-    assert "gpe_grid_opts" in structs and "gpe_real_params" in structs
+    assert "gpe_grid_opts" in structs and "gpe_real_params" in structs and "gpe_ramp_pot" in structs
     for name, fields in structs.items():
         cls = getattr(gpe, name, None)
-        if cls is None:
-            continue
+        assert cls is not None, f"the binding has no {name}"
         assert [f[0] for f in cls._fields_] == fields, name

@@ -623,3 +623,77 @@ def test_numpy_steps_equal_the_c_steps(oracle_mod):
     oa, ob = oracle_mod.observables_np(g, V0, 3.0, psi), oracle_mod.observables(g, V0, 3.0, psi)
     for k in ("norm", "energy", "mu", "e_kin", "e_pot", "e_int"):
         assert abs(oa[k] - ob[k]) <= 1e-13 * max(1.0, abs(ob[k])), k
+
+
+# ----------------------------------------------------------------- multi-stage ramps (Sec. V)
+def stage_problem(oracle_mod, g_=50.0, trap=inputs.Harmonic(1.0, 1.1, 0.9)):
+    box = inputs.cubic_box(28, 0.25)
+    h = (box.hx, box.hy, box.hz)
+    Va = inputs.dense_potential(box, trap)
+    mu = oracle_mod.tf_mu(Va, box.dV, g_, 1.0)
+    rng = np.random.default_rng(70)
+    prof = np.sqrt(np.maximum(mu - Va, 0) / g_) * np.exp(0.3j * rng.normal(size=Va.shape))
+    psi0 = np.where(Va < 5 * mu, prof, 0)
+    psi0 = psi0 / np.sqrt(np.sum(np.abs(psi0) ** 2) * box.dV)
+    return box, h, Va, mu, psi0
+
+
+def test_ramp_stages_with_equal_potentials_chain_into_one_static_evolution(oracle_mod):
+    """Stages and the hold between identical potentials select the same region
+    and must continue one static evolution: 3 + 2 stage steps and a 4-step
+    hold equal 9 RK4 steps in V."""
+    box, h, V, mu, psi0 = stage_problem(oracle_mod)
+    dt, g_ = 0.01, 50.0
+    out, rec = oracle_mod.ramp_stages([V, V, V], h, [3 * dt, 2 * dt], g_, 1.0, dt, psi0, t_hold=4 * dt)
+    assert [r["steps"] for r in rec] == [3, 2, 4]
+    grid = oracle_mod.Grid(V < 5 * mu, h)
+    assert all(r["n_active"] == grid.n and r["cut"] == 5 * mu for r in rec)
+    y, Vc = grid.compact(psi0), grid.compact(V)
+    for k in range(9):
+        y = oracle_mod.rk4_step(grid, Vc, y, g_, 0.0, dt)
+    assert relerr(out, grid.dense(y)) < 1e-12
+    assert abs(rec[-1]["norm_end"] - oracle_mod.observables(grid, Vc, g_, y)["norm"]) < 1e-13
+
+
+def test_ramp_stage_with_a_uniform_shift_is_a_phase(oracle_mod):
+    """V_b = V_a + c: during the stage V(t) = V_a + c t/d, which multiplies the
+    solution by exp(-i c t^2 / 2d) and leaves |psi| alone at any g.  So one
+    stage equals the static evolution in V_a times exp(-i c d / 2), up to the
+    two RK4 errors, which shrink as dt^4."""
+    box, h, Va, mu, psi0 = stage_problem(oracle_mod)
+    c, d, g_ = 3.0, 0.1, 50.0
+    Vb = Va + c
+    errs = []
+    for n in (8, 16):
+        dt = d / n
+        out, rec = oracle_mod.ramp_stages([Va, Vb], h, [d], g_, 1.0, dt, psi0)
+        assert rec[0]["steps"] == n
+        grid = oracle_mod.Grid((Va < rec[0]["cut"]) | (Vb < rec[0]["cut"]), h)
+        assert abs(rec[0]["mu_b"] - rec[0]["mu_a"] - c) < 1e-9      # Eq. (5) shifts with V
+        y, Vc = grid.compact(psi0), grid.compact(Va)
+        for k in range(n):
+            y = oracle_mod.rk4_step(grid, Vc, y, g_, 0.0, dt)
+        errs.append(relerr(out, grid.dense(y * np.exp(-0.5j * c * d))))
+    assert errs[0] < 2e-3 and 12.0 < errs[0] / errs[1] < 20.0, errs     # fourth order
+
+
+def test_ramp_stage_starts_in_its_first_potential(oracle_mod):
+    """Within a stage the potential runs from V_i at t = 0 to V_{i+1} at t = d:
+    the same as a ramp whose knots rise linearly from 0 to 1 over d (not the
+    reverse)."""
+    g_ = 5.0
+    box, h, Va, mu, psi0 = stage_problem(oracle_mod, g_, inputs.Harmonic(2.0, 2.2, 1.8))
+    Vb = inputs.dense_potential(box, inputs.EllipsoidShell(20.0, 2.6, 2.4, 2.2))
+    d, dt = 0.06, 0.01
+    out, rec = oracle_mod.ramp_stages([Va, Vb], h, [d], g_, 1.0, dt, psi0)
+    grid = oracle_mod.Grid((Va < rec[0]["cut"]) | (Vb < rec[0]["cut"]), h)
+    assert rec[0]["n_active"] == grid.n
+    assert grid.n > np.count_nonzero(Va < rec[0]["cut"]) and grid.n > np.count_nonzero(Vb < rec[0]["cut"])
+    A, B = grid.compact(Va), grid.compact(Vb)
+    fwd, rev = grid.compact(psi0), grid.compact(psi0)
+    lin = np.linspace(0.0, 1.0, 16)
+    for k in range(6):
+        fwd = oracle_mod.rk4_step(grid, A, fwd, g_, k * dt, dt, B, lin, d)
+        rev = oracle_mod.rk4_step(grid, A, rev, g_, k * dt, dt, B, lin[::-1].copy(), d)
+    assert relerr(out, grid.dense(fwd)) < 1e-12
+    assert relerr(out, grid.dense(rev)) > 1e-4
