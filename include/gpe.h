@@ -208,8 +208,11 @@ int gpe_grid_potential(const gpe_grid *grid, int slot, double *V);
 int gpe_grid_destroy(gpe_grid *grid);
 
 /* Thomas-Fermi chemical potential (Sec. II A, Eq. (5)): the mu at which
- * sum over the box of max((mu - V)/g, 0) dV equals N, found by bisection on
- * the device.  Synchronous. */
+ * sum over the box of max((mu - V)/g, 0) dV equals N.  That sum is convex and
+ * piecewise linear in mu; Newton's method from above (one pass over the box
+ * per iterate, typically under ten) ends on the exact root of the final
+ * linear piece.  GPE_ERR_ARG for g <= 0, N <= 0 or a non-finite V.
+ * Synchronous. */
 int gpe_tf_mu_dense(const gpe_box *box, const void *V, int V_dtype,
                     int V_on_device, double g, double N, double *mu,
                     gpe_stream stream);

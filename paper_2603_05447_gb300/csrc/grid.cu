@@ -939,59 +939,41 @@ extern "C" int gpe_grid_destroy(gpe_grid *g)
 // ------------------------------------------------------------ Thomas-Fermi mu
 namespace gpe {
 
-// result = {sum over the box of max(mu - V, 0)/g dV, min V, max V}
-__global__ void k_tf_number(VSource src, BoxD box, double mu, double g, double dV, double *partials,
-                            unsigned int *counter, double *result)
+// One pass of the Thomas-Fermi solve: over the cells with V < mu, the sum of
+// V and their count (result[0], result[1]).  Blocks take whole x-rows, so a
+// cell's coordinates need no division; dense sources read V directly.
+__global__ void k_tf_pass(VSource src, BoxD box, double mu, double *partials, unsigned int *counter,
+                          double *result)
 {
-    const int64_t n = box.nx * box.ny * box.nz;
-    double acc[3] = {0.0, 0.0, 0.0};
-    double vmin = 1e300, vmax = -1e300;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = c % box.nx, j = (c / box.nx) % box.ny, k = c / (box.nx * box.ny);
-        double v0, v1;
-        bool sel;
-        cell_values(src, box, i, j, k, v0, v1, sel);
-        if (mu > v0) acc[0] += (mu - v0) / g * dV;
-        vmin = fmin(vmin, v0);
-        vmax = fmax(vmax, v0);
-    }
-    // block min and max of V: reduce them inside the block, then let thread 0
-    // carry them in lanes 1 and 2 of the deterministic reduction so that each
-    // block's values land in partials[b*3 + 1] and partials[b*3 + 2]
-    for (int off = 16; off > 0; off >>= 1) {
-        vmin = fmin(vmin, __shfl_down_sync(0xffffffffu, vmin, off));
-        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, off));
-    }
-    __shared__ double smn[32], smx[32];
-    if ((threadIdx.x & 31) == 0) {
-        smn[threadIdx.x >> 5] = vmin;
-        smx[threadIdx.x >> 5] = vmax;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w) {
-            smn[0] = fmin(smn[0], smn[w]);
-            smx[0] = fmax(smx[0], smx[w]);
-        }
-    }
-    __syncthreads();
-    acc[1] = threadIdx.x == 0 ? smn[0] : 0.0;
-    acc[2] = threadIdx.x == 0 ? smx[0] : 0.0;
-    double tot[3];
-    if (reduce_finish<3>(acc, partials, counter, tot)) {
-        if (threadIdx.x == 0) {
-            double mn = 1e300, mx = -1e300;
-            for (unsigned b = 0; b < gridDim.x; ++b) {
-                mn = fmin(mn, __ldcg(&partials[b * 3 + 1]));
-                mx = fmax(mx, __ldcg(&partials[b * 3 + 2]));
+    double acc[2] = {0.0, 0.0};
+    const int64_t rows = box.ny * box.nz;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t j = r % box.ny, k = r / box.ny;
+        for (int64_t i = threadIdx.x; i < box.nx; i += blockDim.x) {
+            double v0, v1;
+            bool sel;
+            cell_values(src, box, i, j, k, v0, v1, sel);
+            if (v0 < mu) {
+                acc[0] += v0;
+                acc[1] += 1.0;
             }
-            result[0] = tot[0];
-            result[1] = mn;
-            result[2] = mx;
         }
+    }
+    double tot[2];
+    if (reduce_finish<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        result[0] = tot[0];
+        result[1] = tot[1];
     }
 }
 
+// Eq. (5): the mu at which the Thomas-Fermi atom number
+//   F(mu) = sum over the box of max(mu - V, 0) / g dV
+// equals N.  F is convex, increasing and piecewise linear in mu, so Newton's
+// method started above the root stays above it and reaches the root exactly
+// once the set {V < mu} stops changing:
+//   mu <- (g N / dV + sum_{V < mu} V) / #{V < mu}.
+// The first pass takes every cell (mu = +inf), whose line lies below F, so
+// its root already bounds the true one from above.
 static int tf_mu_impl(const gpe_box *box, const VSource &src, double g, double N, double *mu, cudaStream_t st)
 {
     if (!(g > 0)) return fail(GPE_ERR_ARG, "g must be > 0 for the Thomas-Fermi estimate");
@@ -999,39 +981,45 @@ static int tf_mu_impl(const gpe_box *box, const VSource &src, double g, double N
     if (!mu) return fail(GPE_ERR_ARG, "mu is NULL");
     int dev = 0;
     GPE_TRY_CUDA(cudaGetDevice(&dev));
-    const int blocks = sm_count(dev) * 4;
+    const int64_t rows = box->ny * box->nz;
+    const int blocks = (int)std::min<int64_t>(rows, (int64_t)sm_count(dev) * 8);
     RedScratch r;
     GPE_TRY(red_alloc(r, blocks));
-    double *res = nullptr, h[3];
-    int rc = dev_alloc_t(&res, 3);
+    double *res = nullptr, h[2];
+    int rc = dev_alloc_t(&res, 2);
     const BoxD bd = boxd(*box);
     const double dV = box->hx * box->hy * box->hz;
-    auto number = [&](double m, double *out3) -> int {
-        k_tf_number<<<blocks, 256, 0, st>>>(src, bd, m, g, dV, r.partials, r.counter, res);
+    const double target = g * N / dV;
+    auto pass = [&](double m) -> int {
+        k_tf_pass<<<blocks, 256, 0, st>>>(src, bd, m, r.partials, r.counter, res);
         GPE_TRY_CUDA(cudaGetLastError());
-        GPE_TRY_CUDA(cudaMemcpyAsync(out3, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GPE_TRY_CUDA(cudaMemcpyAsync(h, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         GPE_TRY_CUDA(cudaStreamSynchronize(st));
         return GPE_OK;
     };
-    if (rc == GPE_OK) rc = number(0.0, h);
-    if (rc == GPE_OK) {
-        double lo = h[1], hi = h[2];
-        double span = hi - lo > 0 ? hi - lo : 1.0;
-        for (int it = 0; it < 200 && rc == GPE_OK; ++it) {
-            rc = number(hi, h);
-            if (rc != GPE_OK || h[0] >= N) break;
-            hi += span;
-            span *= 2.0;
+    double m = INFINITY;
+    double count = -1.0;
+    for (int it = 0; it < 200 && rc == GPE_OK; ++it) {
+        rc = pass(m);
+        if (rc != GPE_OK) break;
+        if (!(h[1] > 0.0)) {
+            rc = fail(GPE_ERR_ARG, "Thomas-Fermi solve found no cell below mu (V not finite?)");
+            break;
         }
-        for (int it = 0; it < 200 && rc == GPE_OK; ++it) {
-            double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            rc = number(mid, h);
-            if (rc != GPE_OK) break;
-            if (h[0] < N) lo = mid; else hi = mid;
+        const double next = (target + h[0]) / h[1];
+        const bool same_set = h[1] == count;
+        count = h[1];
+        if (!std::isfinite(next)) {
+            rc = fail(GPE_ERR_ARG, "Thomas-Fermi solve: non-finite mu (V not finite?)");
+            break;
         }
-        *mu = 0.5 * (lo + hi);
+        if (same_set || !(next < m)) {
+            m = std::min(m, next);
+            break;
+        }
+        m = next;
     }
+    if (rc == GPE_OK) *mu = m;
     dev_free(res);
     red_free(r);
     return rc;

@@ -442,3 +442,19 @@ def test_tf_mu_matches_oracle():
     pot = gpe.make_potential(gpe.GPE_POT_HARMONIC, 1, 1, 1)
     mu_an = gpe.gpe_tf_mu_analytic(gb, pot, 500.0, 1.0)
     assert abs(mu_an - mu_orc) <= 1e-10 * mu_orc
+
+
+@pytest.mark.parametrize("name", ["SHELL_64", "SHELL_96"])
+def test_tf_mu_on_shells_matches_oracle_and_holds_N_atoms(name):
+    wl = getattr(inputs, name)
+    b = wl.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    V = inputs.dense_potential(b, wl.potential)
+    mu_orc = oracle.tf_mu(V, b.dV, wl.g, wl.N)
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    for mu in (gpe.gpe_tf_mu_dense(gb, V, wl.g, wl.N), gpe.gpe_tf_mu_analytic(gb, pot, wl.g, wl.N),
+               gpe.gpe_tf_mu_dense(gb, np.ascontiguousarray(V.astype(np.float32)), wl.g, wl.N)):
+        assert abs(mu - mu_orc) <= 1e-6 * mu_orc
+    mu = gpe.gpe_tf_mu_dense(gb, V, wl.g, wl.N)
+    assert abs(mu - mu_orc) <= 1e-12 * mu_orc
+    assert abs(np.sum(np.maximum(mu - V, 0)) / wl.g * b.dV - wl.N) < 1e-10
