@@ -364,7 +364,7 @@ def ramp_loss_and_grad(grid: Grid, V0, V1, knots, T, g, dt, nsteps, psi0, psi_ta
     return loss, grad, y
 
 
-def ramp_stages(Vs, h, durations, g, N, dt, psi0, cut_factor=5.0, t_hold=0.0, method="RK4"):
+def ramp_stages(Vs, h, durations, g, N, dt, psi0, cut_factor=5.0, t_hold=0.0, method="RK4", stencil=7):
     """Multi-stage ramp of Sec. V through the dense potentials Vs[0..M].
 
     Stage i interpolates linearly in time from Vs[i] to Vs[i+1] over
@@ -376,6 +376,7 @@ def ramp_stages(Vs, h, durations, g, N, dt, psi0, cut_factor=5.0, t_hold=0.0, me
     The stage takes ceil(d / dt) equal steps.  With t_hold > 0 a hold in the
     last potential follows on {Vs[-1] < cut_factor * mu_M}.
 
+    stencil 19 takes the numpy steps with App. B's Laplacian.
     psi0 is a dense box array (zero outside its own region).  Returns the
     final dense psi and one record per stage (mu_a, mu_b, cut, n_active,
     steps, dt, norm_kept, norm_end).
@@ -408,7 +409,10 @@ def ramp_stages(Vs, h, durations, g, N, dt, psi0, cut_factor=5.0, t_hold=0.0, me
         else:
             V0, V1, knots = grid.compact(Vs[i]), grid.compact(Vs[i + 1]), np.array([0.0, 1.0])
         for k in range(n):
-            y = rk_step(grid, V0, y, g, k * dts, dts, method, V1, knots, d)
+            if stencil == 7:
+                y = rk_step(grid, V0, y, g, k * dts, dts, method, V1, knots, d)
+            else:
+                y = rk_step_np(grid, V0, y, g, k * dts, dts, method, V1, knots, d, stencil)
         psi = grid.dense(y)
         records.append(dict(mu_a=mu_a, mu_b=mu_b, cut=cut, n_active=grid.n, steps=n, dt=dts,
                             norm_kept=norm_kept, norm_end=float(np.sum(np.abs(y) ** 2) * dV)))

@@ -62,14 +62,14 @@ def expected():
     return Vs, psi0, mu0, out, rec
 
 
-def run(Vs, psi0, mu0, dtype, kind, opts=None, first_brick=(8, 8, 8)):
+def run(Vs, psi0, mu0, dtype, kind, opts=None, first_brick=(8, 8, 8), integrator=gpe.GPE_RK4, dt=DT):
     cdt = np.complex128 if dtype == gpe.GPE_C128 else np.complex64
     g0 = gpe.gpe_grid_create_analytic(gbox(), analytic(POTS[0]), 5 * mu0, gpe.make_opts(first_brick))
     s0 = gpe.gpe_state_create(g0, dtype)
     try:
         gpe.gpe_state_load(s0, np.ascontiguousarray(psi0, dtype=cdt), gpe.GPE_LAYOUT_DENSE)
         pots = [analytic(p) for p in POTS] if kind == "analytic" else [np.ascontiguousarray(V) for V in Vs]
-        params = gpe.stage_params(G, N, DT, 5.0, T_HOLD)
+        params = gpe.stage_params(G, N, dt, 5.0, T_HOLD, integrator)
         grid, st, rep = gpe.gpe_ramp_stages(s0, pots, DURATIONS, params, opts)
     finally:
         gpe.gpe_state_destroy(s0)
@@ -113,6 +113,22 @@ def test_stage_regions_change_and_grid_options_are_inherited(expected):
     assert len({r["n_active"] for r in rec}) == 3
     got, rep, info = run(Vs, psi0, mu0, gpe.GPE_C128, "analytic", None, first_brick=(8, 4, 4))
     assert (info.bx, info.by, info.bz) == (8, 4, 4)
+    assert rel_l2(got, want) < 1e-10
+
+
+@pytest.mark.parametrize("method,stencil", [("RKHE3", 7), ("RKCK", 7), ("RK4", 19)])
+def test_stages_with_other_integrators_and_the_19_point_stencil(expected, method, stencil):
+    """The stage loop passes its integrator and the grid options through:
+    RKHE3 and RKCK (App. A) and App. B's 19-point Laplacian.  RKCK takes a
+    shorter step: its accepted range on the imaginary axis is narrower."""
+    Vs, psi0, mu0, _, _ = expected
+    dt = DT / 2 if method == "RKCK" else DT
+    want, rec = oracle.ramp_stages(Vs, (BOX.hx, BOX.hy, BOX.hz), DURATIONS, G, N, dt, psi0, t_hold=T_HOLD,
+                                   method=method, stencil=stencil)
+    integ = {"RK4": gpe.GPE_RK4, "RKHE3": gpe.GPE_RKHE3, "RKCK": gpe.GPE_RKCK}[method]
+    got, rep, info = run(Vs, psi0, mu0, gpe.GPE_C128, "analytic", gpe.make_opts((8, 8, 4), stencil=stencil),
+                         integrator=integ, dt=dt)
+    assert [r["n_active"] for r in rep] == [o["n_active"] for o in rec]
     assert rel_l2(got, want) < 1e-10
 
 
