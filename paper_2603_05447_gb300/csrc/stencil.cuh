@@ -37,8 +37,11 @@ struct KernelCfg {
 #define GPE_MINB_D 3
 #endif
 #define GPE_BOUNDS(R) __launch_bounds__(KernelCfg<R>::THREADS, (min_blocks<R, BX, BY, BZ>()))
-// kernels templated on the stencil NP: the 19-point form needs more registers
-#define GPE_BOUNDS_NP(R) __launch_bounds__(KernelCfg<R>::THREADS, (NP == 19 ? 2 : min_blocks<R, BX, BY, BZ>()))
+// kernels templated on the stencil NP: the 19-point form needs more
+// registers; in single precision three blocks an SM (80 registers) beat two
+// (about 105) despite a few spilled bytes in some variants
+#define GPE_BOUNDS_NP(R) \
+    __launch_bounds__(KernelCfg<R>::THREADS, (NP == 19 ? (sizeof(R) == 4 ? 3 : 2) : min_blocks<R, BX, BY, BZ>()))
 
 // ------------------------------------------------------------ packed layout
 // supported brick shapes (shape id, BX, BY, BZ)
