@@ -444,6 +444,41 @@ def test_tf_mu_matches_oracle():
     assert abs(mu_an - mu_orc) <= 1e-10 * mu_orc
 
 
+def test_tf_mu_closed_forms():
+    """A flat potential V = c fills the box: mu = c + g N / (n dV).  A
+    potential of two levels puts every atom on the lower level while
+    mu - lo < hi - lo."""
+    box = inputs.Box(37, 29, 23, 0.3, 0.25, 0.2)
+    gb = gpe.make_box(box.nx, box.ny, box.nz, box.hx, box.hy, box.hz)
+    n = box.nx * box.ny * box.nz
+    V = np.full(box.shape, 1.75)
+    mu = gpe.gpe_tf_mu_dense(gb, V, 3.0, 2.0)
+    assert abs(mu - (1.75 + 3.0 * 2.0 / (n * box.dV))) <= 1e-14 * mu
+    V2 = np.where(np.arange(n).reshape(box.shape) % 3 == 0, 0.5, 1e6)
+    m = np.count_nonzero(V2 == 0.5)
+    mu2 = gpe.gpe_tf_mu_dense(gb, V2, 3.0, 2.0)
+    assert abs(mu2 - (0.5 + 3.0 * 2.0 / (m * box.dV))) <= 1e-14 * mu2
+
+
+def test_blend_dense_grid_is_the_union_of_both_regions():
+    box = inputs.Box(45, 39, 35, 0.25, 0.25, 0.25)
+    gb = gpe.make_box(box.nx, box.ny, box.nz, box.hx, box.hy, box.hz)
+    V0 = inputs.dense_potential(box, inputs.Harmonic(2.0, 2.2, 1.8))
+    V1 = inputs.dense_potential(box, inputs.EllipsoidShell(3.0, 1.6, 1.5, 1.4))
+    grid = gpe.gpe_grid_create_blend_dense(gb, V0, V1, 6.0, 2.0, gpe.make_opts((8, 8, 4)))
+    try:
+        info = gpe.gpe_grid_get_info(grid)
+        region = (V0 < 6.0) | (V1 < 2.0)
+        assert info.n_active == np.count_nonzero(region) and info.n_slots == 2
+        idx, i, j, k = gpe.packed_coords(grid)
+        assert np.array_equal(np.sort(i + box.nx * (j + box.ny * k)), np.flatnonzero(region.ravel()))
+        for slot, V in ((0, V0), (1, V1)):
+            assert np.array_equal(gpe.gpe_grid_potential(grid, slot)[idx], V[k, j, i])
+        assert info.v_max == max(V0[region].max(), V1[region].max())
+    finally:
+        gpe.gpe_grid_destroy(grid)
+
+
 @pytest.mark.parametrize("name", ["SHELL_64", "SHELL_96"])
 def test_tf_mu_on_shells_matches_oracle_and_holds_N_atoms(name):
     wl = getattr(inputs, name)
