@@ -132,6 +132,34 @@ def test_stages_with_other_integrators_and_the_19_point_stencil(expected, method
     assert rel_l2(got, want) < 1e-10
 
 
+def test_stages_without_a_report_give_the_same_state(expected):
+    """report = NULL skips the observables; the result is the same."""
+    import ctypes
+    Vs, psi0, mu0, want, rec = expected
+    g0 = gpe.gpe_grid_create_analytic(gbox(), analytic(POTS[0]), 5 * mu0)
+    s0 = gpe.gpe_state_create(g0, gpe.GPE_C128)
+    try:
+        gpe.gpe_state_load(s0, np.ascontiguousarray(psi0), gpe.GPE_LAYOUT_DENSE)
+        pots = (gpe.gpe_ramp_pot * 3)()
+        keep = [analytic(p) for p in POTS]
+        for i, P in enumerate(keep):
+            pots[i].analytic = ctypes.pointer(P)
+        dur = (ctypes.c_double * 2)(*DURATIONS)
+        params = gpe.stage_params(G, N, DT, 5.0, T_HOLD)
+        grid, st = ctypes.c_void_p(), ctypes.c_void_p()
+        rc = gpe.load().gpe_ramp_stages(s0, pots, 3, dur, ctypes.byref(params), None, ctypes.byref(grid),
+                                        ctypes.byref(st), None, gpe.stream_handle())
+        assert rc == gpe.GPE_OK, gpe.last_error()
+        out = np.zeros(BOX.shape, np.complex128)
+        gpe.gpe_state_store(st.value, out, gpe.GPE_LAYOUT_DENSE)
+        gpe.gpe_state_destroy(st.value)
+        gpe.gpe_grid_destroy(grid.value)
+        assert rel_l2(out, want) < 1e-10
+    finally:
+        gpe.gpe_state_destroy(s0)
+        gpe.gpe_grid_destroy(g0)
+
+
 def test_stage_argument_errors(expected):
     Vs, psi0, mu0, _, _ = expected
     g0 = gpe.gpe_grid_create_analytic(gbox(), analytic(POTS[0]), 5 * mu0)
