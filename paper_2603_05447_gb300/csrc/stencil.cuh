@@ -166,18 +166,18 @@ __device__ __forceinline__ CT vadd(const CT &a, const CT &b)
         return a + b;
     }
 }
-// w (e - 2 f + 4 c): one mixed second difference of App. B's 19-point
-// stencil from its edge sum e, face sum f and centre c
+// L + wxy exy + wxz exz + wyz eyz: the edge terms of App. B's 19-point
+// stencil added to its face-and-centre part
 template <typename CT, typename R>
-__device__ __forceinline__ CT mixv(const CT &e, const CT &f, const CT &c, R w)
+__device__ __forceinline__ CT edgev(const CT &L, const CT &exy, const CT &exz, const CT &eyz, R wxy, R wxz, R wyz)
 {
     if constexpr (is_cplx<CT>()) {
         CT o;
-        o.x = w * (e.x - (R)2 * f.x + (R)4 * c.x);
-        o.y = w * (e.y - (R)2 * f.y + (R)4 * c.y);
+        o.x = L.x + wxy * exy.x + wxz * exz.x + wyz * eyz.x;
+        o.y = L.y + wxy * exy.y + wxz * exz.y + wyz * eyz.y;
         return o;
     } else {
-        return w * (e - (R)2 * f + (R)4 * c);
+        return L + wxy * exy + wxz * exz + wyz * eyz;
     }
 }
 // one component of the 7-point Laplacian (Eq. (B1)) from opposite-neighbour
@@ -656,16 +656,24 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
         ws.get(sl + W::PLANE, zp);
         const CT xm = hx == 0 ? ws.xlo[hrow] : ws.last(sl - 1);
         const CT xp = hx == S::SX - 1 ? ws.xhi[hrow] : ws.first(sl + 1);
+        if constexpr (NP != 19) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const CT l = i == 0 ? xm : c[i - 1];
-            const CT rr = i == 3 ? xp : c[i + 1];
-            L[i] = lapv(rr, l, yp[i], ym[i], zp[i], zm[i], c[i], ihx2, ihy2, ihz2, c6);
-        }
-        if constexpr (NP == 19) {
-            // App. B: + w_ab (edges_ab - 2 faces_ab + 4 c) per plane ab, with
-            // w_ab = (h_a^2 + h_b^2) / (12 h_a^2 h_b^2) = (1/h_a^2 + 1/h_b^2) / 12
+            for (int i = 0; i < 4; ++i) {
+                const CT l = i == 0 ? xm : c[i - 1];
+                const CT rr = i == 3 ? xp : c[i + 1];
+                L[i] = lapv(rr, l, yp[i], ym[i], zp[i], zm[i], c[i], ihx2, ihy2, ihz2, c6);
+            }
+        } else {
+            // App. B: the 7-point part plus w_ab (edges_ab - 2 faces_ab + 4 c)
+            // per plane ab, w_ab = (h_a^2 + h_b^2) / (12 h_a^2 h_b^2)
+            // = (1/h_a^2 + 1/h_b^2) / 12.  Each face pair lies in two planes,
+            // so the face and centre terms fold into the 7-point form with
+            //   x: 1/hx^2 - 2 (wxy + wxz), y: 1/hy^2 - 2 (wxy + wyz),
+            //   z: 1/hz^2 - 2 (wxz + wyz), centre: c6 - 4 (wxy + wxz + wyz),
+            // and only the three edge sums remain: + wxy exy + wxz exz + wyz eyz.
             const R wxy = (ihx2 + ihy2) / (R)12, wxz = (ihx2 + ihz2) / (R)12, wyz = (ihy2 + ihz2) / (R)12;
+            const R ax = ihx2 - (R)2 * (wxy + wxz), ay = ihy2 - (R)2 * (wxy + wyz), az = ihz2 - (R)2 * (wxz + wyz);
+            const R c19 = c6 - (R)4 * (wxy + wxz + wyz);
             const int row = sl / S::SX, y = row % W::TY - 1, z = row / W::TY - 1;
             auto left = [&](int s2, int yy, int zz) { return hx == 0 ? ws.xlo[W::h(yy, zz)] : ws.last(s2 - 1); };
             auto right = [&](int s2, int yy, int zz) {
@@ -693,10 +701,8 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
                                     vadd(i == 0 ? ypl : yp[i - 1], i == 3 ? ypr : yp[i + 1]));
                 const CT exz = vadd(vadd(i == 0 ? zml : zm[i - 1], i == 3 ? zmr : zm[i + 1]),
                                     vadd(i == 0 ? zpl : zp[i - 1], i == 3 ? zpr : zp[i + 1]));
-                const CT lr = vadd(l, rr);
-                L[i] = vadd(L[i], mixv(exy, vadd(lr, vadd(ym[i], yp[i])), c[i], wxy));
-                L[i] = vadd(L[i], mixv(exz, vadd(lr, vadd(zm[i], zp[i])), c[i], wxz));
-                L[i] = vadd(L[i], mixv(eyz[i], vadd(vadd(ym[i], yp[i]), vadd(zm[i], zp[i])), c[i], wyz));
+                L[i] = edgev(lapv(rr, l, yp[i], ym[i], zp[i], zm[i], c[i], ax, ay, az, c19), exy, exz, eyz[i], wxy,
+                             wxz, wyz);
             }
         }
         body(R0.off + 4u * (uint32_t)r, pre, c, L);
