@@ -140,3 +140,37 @@ def test_itp_full_size_sampled_up_to_one_factor(big, dtype, tol):
     factor = np.median(np.real(got[big_] / ref[big_]))
     assert 0.9 < factor < 1.1
     assert np.all(np.abs(got - factor * ref) <= tol * scl * factor)
+
+
+def test_rk4_19_point_full_size_sampled(big):
+    """App. B's 19-point stencil on the same shell, same launch configuration:
+    its grid packs the cells exactly as the 7-point grid does (the stencil
+    only adds edge records), so the samples reuse the layout.  A cell's new
+    value depends on cells within Chebyshev distance 4, inside the patch."""
+    wl, tol = big["wl"], 2e-6
+    b = wl.box
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    grid = gpe.gpe_grid_create_analytic(gpe.make_box(b.nx, b.ny, b.nz, b.hx), pot, wl.V_cut,
+                                        gpe.make_opts(big["shape"], stencil=19))
+    try:
+        info = gpe.gpe_grid_get_info(grid)
+        assert info.n_packed == big["info"].n_packed and info.n_active == big["info"].n_active
+        st = gpe.gpe_state_create(grid, gpe.GPE_C64)
+        try:
+            before = np.ascontiguousarray(big["psi0"].astype(np.complex64))
+            gpe.gpe_state_load(st, before, gpe.GPE_LAYOUT_COMPACT)
+            gpe.gpe_step_real(st, gpe.real_params(wl.g, wl.stable_dt()), 1)
+            after = np.zeros_like(before)
+            gpe.gpe_state_store(st, after, gpe.GPE_LAYOUT_COMPACT)
+        finally:
+            gpe.gpe_state_destroy(st)
+    finally:
+        gpe.gpe_grid_destroy(grid)
+    before, after = before.astype(np.complex128), after.astype(np.complex128)
+    for (i, j, k) in samples(big, 13):
+        m, idx = patch(big, i, j, k)
+        g = oracle.Grid(m, wl.box.hx)
+        y = oracle.rk_step_np(g, big["V"][idx[m]], before[idx[m]], wl.g, 0.0, wl.stable_dt(), "RK4", stencil=19)
+        c = np.flatnonzero(np.all(g.ijk() == HALF, axis=1))[0]
+        scale = np.max(np.abs(before[idx[m]]))
+        assert abs(after[idx[HALF, HALF, HALF]] - y[c]) <= tol * scale, (i, j, k)
