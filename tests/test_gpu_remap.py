@@ -37,22 +37,27 @@ def gbox():
     return gpe.make_box(BOX.nx, BOX.ny, BOX.nz, BOX.hx, BOX.hy, BOX.hz)
 
 
-@pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64])
+NPT = {gpe.GPE_C128: np.complex128, gpe.GPE_C64: np.complex64, gpe.GPE_R64: np.float64, gpe.GPE_R32: np.float32}
+
+
+@pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64, gpe.GPE_R64, gpe.GPE_R32])
 @pytest.mark.parametrize("bricks", [((8, 8, 8), (8, 8, 8)), ((8, 8, 4), (8, 4, 4)),
                                     ((8, 4, 4), (8, 8, 8))])
 def test_remap_keeps_common_cells_and_zeroes_the_rest(dtype, bricks):
     V_a, m_a = region(inputs.EllipsoidShell(30.0, 0.9, 0.8, 0.7), 3.0)      # stage i
     V_b, m_b = region(inputs.EllipsoidShell(30.0, 0.95, 0.85, 0.75), 4.0)   # stage i + 1
     assert (m_a & m_b).any() and (m_a & ~m_b).any() and (m_b & ~m_a).any()
-    cdt = np.complex128 if dtype == gpe.GPE_C128 else np.complex64
-    psi = seeded_psi(7).astype(cdt)
+    cdt = NPT[dtype]
+    psi = (seeded_psi(7).real if dtype in (gpe.GPE_R64, gpe.GPE_R32) else seeded_psi(7)).astype(cdt)
     ga = gpe.gpe_grid_create_dense(gbox(), V_a, 3.0, gpe.make_opts(bricks[0]))
     gb = gpe.gpe_grid_create_dense(gbox(), V_b, 4.0, gpe.make_opts(bricks[1], order=gpe.GPE_ORDER_MORTON))
     sa = gpe.gpe_state_create(ga, dtype)
     sb = gpe.gpe_state_create(gb, dtype)
     try:
         gpe.gpe_state_load(sa, np.ascontiguousarray(psi), gpe.GPE_LAYOUT_DENSE)
-        gpe.gpe_state_load(sb, np.ascontiguousarray(seeded_psi(8).astype(cdt)), gpe.GPE_LAYOUT_DENSE)
+        other = seeded_psi(8)
+        other = other.real if dtype in (gpe.GPE_R64, gpe.GPE_R32) else other
+        gpe.gpe_state_load(sb, np.ascontiguousarray(other.astype(cdt)), gpe.GPE_LAYOUT_DENSE)
         gpe.gpe_state_remap(sb, sa)
         out = np.zeros(BOX.shape, cdt)
         gpe.gpe_state_store(sb, out, gpe.GPE_LAYOUT_DENSE)

@@ -132,6 +132,14 @@ def test_stages_with_other_integrators_and_the_19_point_stencil(expected, method
     assert rel_l2(got, want) < 1e-10
 
 
+@pytest.mark.parametrize("sched", [gpe.GPE_SCHED_WAVE, gpe.GPE_SCHED_WAVE2])
+def test_stages_on_the_wavefront_schedules_are_bit_identical(expected, sched):
+    Vs, psi0, mu0, _, _ = expected
+    ref, _, _ = run(Vs, psi0, mu0, gpe.GPE_C64, "analytic", gpe.make_opts((8, 8, 4)))
+    got, _, _ = run(Vs, psi0, mu0, gpe.GPE_C64, "analytic", gpe.make_opts((8, 8, 4), sched=sched))
+    assert np.array_equal(got, ref)
+
+
 def test_stages_without_a_report_give_the_same_state(expected):
     """report = NULL skips the observables; the result is the same."""
     import ctypes

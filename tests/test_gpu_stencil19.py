@@ -22,7 +22,7 @@ def lib():
     return gpe.load()
 
 
-NPT = {gpe.GPE_C128: np.complex128, gpe.GPE_C64: np.complex64, gpe.GPE_R64: np.float64}
+NPT = {gpe.GPE_C128: np.complex128, gpe.GPE_C64: np.complex64, gpe.GPE_R64: np.float64, gpe.GPE_R32: np.float32}
 
 
 class G19:
@@ -37,7 +37,7 @@ class G19:
             gpe.gpe_grid_set_potential(self.grid, 1, case.V1)
         self.st = gpe.gpe_state_create(self.grid, dtype)
         psi = case.psi if psi is None else psi
-        arr = psi.real if dtype == gpe.GPE_R64 else psi
+        arr = psi.real if dtype in (gpe.GPE_R64, gpe.GPE_R32) else psi
         gpe.gpe_state_load(self.st, np.ascontiguousarray(arr.astype(NPT[dtype])), gpe.GPE_LAYOUT_DENSE)
 
     def dense(self):
@@ -131,6 +131,24 @@ def test_itp_matches_oracle(dtype):
         for _ in range(4):
             y, _ = oracle.itp_step_np(og, og.compact(case.V), y, case.g, case.dt, 1.0, stencil=19)
         assert rel_l2(G.dense(), og.dense(y)) <= 1e-12
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("dtype", [gpe.GPE_C64, gpe.GPE_R32])
+def test_itp_single_precision_matches_oracle(dtype):
+    """From the same single-precision input, four steps: a few roundings of
+    6e-8 per pass and step."""
+    case = ragged_shell()
+    psi = np.abs(case.psi).astype(NPT[dtype]).astype(np.complex128)
+    G = G19(case, dtype, brick=(8, 8, 4), psi=psi)
+    try:
+        gpe.gpe_step_imag(G.st, gpe.gpe_imag_params(case.g, case.dt, 1.0), 4)
+        og = ogrid(case)
+        y = og.compact(psi)
+        for _ in range(4):
+            y, _ = oracle.itp_step_np(og, og.compact(case.V), y, case.g, case.dt, 1.0, stencil=19)
+        assert rel_l2(G.dense(), og.dense(y)) <= 1e-5
     finally:
         G.close()
 
