@@ -124,10 +124,13 @@ __global__ void GPE_BOUNDS_NP(R) k_itp_b(const ItpArgs<R, CT> a, const GridView 
     }
 }
 
+// the pending renormalisation applied at the end of a call, rounded exactly as
+// the next step's load would apply it (factor in the state's precision), so
+// that a run split across calls or resumed from a dump is bit-identical
 template <typename CT>
 __global__ void k_apply_scale(CT *psi, int64_t n, const double *scalars)
 {
-    const double sc = scalars[0];
+    const auto sc = (typename RealOf<CT>::T)scalars[0];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         psi[s] = scale(psi[s], sc);
     }
