@@ -106,6 +106,30 @@ def test_stages_match_the_oracle(expected, kind, dtype):
     assert rel_l2(got, want) < tol
 
 
+def test_stages_with_float32_device_potentials(expected):
+    """Dense single-precision potentials already on the device (the form a
+    large precomputed ramp takes): the oracle runs on the same rounded
+    potentials, so regions and results match as before."""
+    Vs, psi0, mu0, _, _ = expected
+    Vs32 = [V.astype(np.float32).astype(np.float64) for V in Vs]
+    want, rec = oracle.ramp_stages(Vs32, (BOX.hx, BOX.hy, BOX.hz), DURATIONS, G, N, DT, psi0, t_hold=T_HOLD)
+    dev = [torch.from_numpy(V.astype(np.float32)).cuda() for V in Vs]
+    g0 = gpe.gpe_grid_create_analytic(gbox(), analytic(POTS[0]), 5 * mu0)
+    s0 = gpe.gpe_state_create(g0, gpe.GPE_C128)
+    try:
+        gpe.gpe_state_load(s0, np.ascontiguousarray(psi0), gpe.GPE_LAYOUT_DENSE)
+        grid, st, rep = gpe.gpe_ramp_stages(s0, dev, DURATIONS, gpe.stage_params(G, N, DT, 5.0, T_HOLD))
+        out = np.zeros(BOX.shape, np.complex128)
+        gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_DENSE)
+        gpe.gpe_state_destroy(st)
+        gpe.gpe_grid_destroy(grid)
+    finally:
+        gpe.gpe_state_destroy(s0)
+        gpe.gpe_grid_destroy(g0)
+    assert [r["n_active"] for r in rep] == [o["n_active"] for o in rec]
+    assert rel_l2(out, want) < 1e-10
+
+
 def test_stage_regions_change_and_grid_options_are_inherited(expected):
     """The regions differ from stage to stage (the remap does work), and with
     no options the stage grids take the initial grid's brick shape."""
