@@ -350,6 +350,19 @@ typedef struct gpe_obs {
 int gpe_observables(const gpe_state *st, double g, double s_blend,
                     gpe_obs *out, gpe_stream stream);
 
+/* Real-time steps with an observables trace: nsteps steps as gpe_step_real
+ * (same parameters, from time t0), with the observables of gpe_observables
+ * taken after every `every` steps and after the last one (potential energy
+ * at s(t) of that time for a ramp).  log (host, ceil(nsteps / every)
+ * entries) receives them in order and *n_logged how many were written.
+ * A trace point that finds a non-finite cell ends the run there with
+ * GPE_ERR_NONFINITE (that entry included).  The same steps and the same
+ * reductions as separate calls, so the results are bit-identical to them.
+ * Synchronous at each trace point. */
+int gpe_step_real_traced(gpe_state *st, const gpe_real_params *p,
+                         int64_t nsteps, double t0, int64_t every,
+                         gpe_obs *log, int64_t *n_logged, gpe_stream stream);
+
 /* out = <a|b> = sum conj(a) b dV as (re, im).  Synchronous. */
 int gpe_overlap(const gpe_state *a, const gpe_state *b, double out[2],
                 gpe_stream stream);

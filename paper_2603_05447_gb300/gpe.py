@@ -160,6 +160,8 @@ _SIGS = {
     "gpe_step_real": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, _P]),
     "gpe_observables": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(gpe_obs), _P]),
     "gpe_overlap": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P]),
+    "gpe_step_real_traced": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, C.c_int64,
+                                       C.POINTER(gpe_obs), C.POINTER(C.c_int64), _P]),
     "gpe_state_set_graph": (C.c_int, [_P, C.c_int]),
     "gpe_wait_selftest": (C.c_int, [C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "gpe_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P)]),
@@ -478,6 +480,19 @@ def gpe_observables(state, g, s_blend=0.0, stream=None, check=True) -> dict:
     if rc != GPE_OK and (check or rc != GPE_ERR_NONFINITE):
         raise GpeError(rc, last_error())
     return o.asdict()
+
+
+def gpe_step_real_traced(state, params, nsteps, every, t0=0.0, stream=None, check=True) -> list:
+    """gpe_step_real with the observables every `every` steps: a list of
+    dicts (the trace up to a non-finite point when check is False)."""
+    n_max = max(1, -(-int(nsteps) // int(every))) if every > 0 else 1
+    log = (gpe_obs * n_max)()
+    n = C.c_int64()
+    rc = load().gpe_step_real_traced(state, C.byref(params), int(nsteps), float(t0), int(every), log,
+                                     C.byref(n), stream_handle(stream))
+    if rc != GPE_OK and (check or rc != GPE_ERR_NONFINITE):
+        raise GpeError(rc, last_error())
+    return [log[i].asdict() for i in range(n.value)]
 
 
 def gpe_overlap(a, b, stream=None) -> complex:

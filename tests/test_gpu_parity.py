@@ -526,3 +526,52 @@ def test_checkpoint_and_resume_are_bit_exact(dtype):
             gpe.gpe_step_imag(A.state, q, 4)
             resumed = A.dense()
     assert np.array_equal(resumed, straight)
+
+
+# ----------------------------------------------------------------- observables trace
+def test_traced_steps_equal_separate_calls_and_the_oracle():
+    case = ragged_shell()
+    p = gpe.real_params(case.g, case.dt)
+    with Gpu(case) as A:
+        log = gpe.gpe_step_real_traced(A.state, p, 10, 4)
+    with Gpu(case) as B:
+        sep = []
+        for n in (4, 4, 2):
+            gpe.gpe_step_real(B.state, p, n)
+            sep.append(gpe.gpe_observables(B.state, case.g))
+    assert log == sep
+    og = oracle_grid(case)
+    y, V = og.compact(case.psi), og.compact(case.V)
+    for _ in range(10):
+        y = oracle.rk4_step(og, V, y, case.g, 0.0, case.dt)
+    o = oracle.observables(og, V, case.g, y)
+    for k in ("norm", "energy", "mu"):
+        assert abs(log[-1][k] - o[k]) <= 1e-12 * abs(o[k]), k
+
+
+def test_traced_ramp_uses_the_blend_at_each_trace_time():
+    case = ramp_case()
+    p = gpe.real_params(case.g, case.dt, gpe.GPE_V_BLEND, case.knots, case.T)
+    with Gpu(case) as A:
+        log = gpe.gpe_step_real_traced(A.state, p, 9, 3, t0=0.5 * case.dt)
+    with Gpu(case) as B:
+        for i, n in enumerate((3, 3, 3)):
+            gpe.gpe_step_real(B.state, p, n, 0.5 * case.dt + 3 * i * case.dt)
+            s = oracle.ramp_s(case.knots, case.T, 0.5 * case.dt + 3 * (i + 1) * case.dt)
+            o = gpe.gpe_observables(B.state, case.g, s)
+            for k in ("norm", "e_kin", "e_pot", "e_int"):
+                assert abs(log[i][k] - o[k]) <= 1e-14 * abs(o[k]), (i, k)
+
+
+def test_traced_steps_stop_at_a_nonfinite_point():
+    case = ragged_shell()
+    psi = case.psi.copy()
+    k, j, i = np.argwhere(case.mask)[len(np.argwhere(case.mask)) // 2]
+    psi[k, j, i] = np.nan
+    with Gpu(case) as A:
+        A.load(psi)
+        with pytest.raises(gpe.GpeError) as e:
+            gpe.gpe_step_real_traced(A.state, gpe.real_params(case.g, case.dt), 10, 4)
+        assert e.value.code == gpe.GPE_ERR_NONFINITE
+        log = gpe.gpe_step_real_traced(A.state, gpe.real_params(case.g, case.dt), 10, 4, check=False)
+        assert len(log) == 1 and log[0]["nonfinite"] > 0
