@@ -112,14 +112,15 @@ __global__ void k_batch_norm_finish(ShellParams *sh, const double *part, const i
     }
 }
 
-// apply each shell's pending factor to its bricks, then reset it to 1
+// apply each shell's pending factor to its bricks (rounded to the state's
+// precision, as the next load would apply it), then reset it to 1
 template <typename CT>
 __global__ void k_batch_apply_scale(CT *psi, const BrickRec *rec, const ShellParams *sh, int64_t nb, int nseg)
 {
     for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
         const BrickRec r = rec[b];
         const ShellParams &P = sh[shell_of(r)];
-        const double sc = P.scale;
+        const auto sc = (typename RealOf<CT>::T)P.scale;
         int n = 0;
         for (int w = 0; w < 4; ++w) n += __popc(r.m[w]);
         for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) {
