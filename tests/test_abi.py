@@ -103,3 +103,18 @@ def test_binding_structs_match_the_header_field_by_field():
         cls = getattr(gpe, name, None)
         assert cls is not None, f"the binding has no {name}"
         assert [f[0] for f in cls._fields_] == fields, name
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as C99 and as C++ (no torch or CUDA types
+    in the signatures)."""
+    import shutil
+    import subprocess
+    for cc, std, ext in (("gcc", "-std=c99", "c"), ("g++", "-std=c++17", "cpp")):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not available")
+        src = tmp_path / f"use.{ext}"
+        src.write_text('#include "gpe.h"\nint main(void) { return 0; }\n')
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                            "-I" + os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
