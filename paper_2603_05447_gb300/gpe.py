@@ -578,6 +578,8 @@ def gpe_ramp_stages(psi0, pots, durations, params, opts=None, stream=None):
     dense float64/float32 array, all of one kind); returns (grid, state,
     reports).  The caller destroys the state, then the grid."""
     n = len(pots)
+    if len(durations) != max(n - 1, 0):
+        raise ValueError(f"{n} potentials need {max(n - 1, 0)} stage durations, got {len(durations)}")
     arr = (gpe_ramp_pot * n)()
     keep = []
     for i, P in enumerate(pots):
