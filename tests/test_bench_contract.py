@@ -28,3 +28,16 @@ def test_reference_arm_prints_one_contract_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "workload" in line["config"]
+
+
+def test_committed_traffic_profile_matches_the_current_kernels():
+    """bench.py reports the DRAM traffic of the committed ncu capture only
+    while the stage kernels' sources hash to the value recorded with it; a
+    kernel change must come with a new capture."""
+    sys.path.insert(0, ROOT)
+    import bench
+    t = json.load(open(bench.TRAFFIC_FILE))
+    assert t["kernel_source_hash"] == bench.kernel_source_hash()
+    assert t["bytes_per_step"] == sum(t["dram_bytes_per_stage"])
+    # at least the compulsory 112 B per stored cell and step of the staged RK4
+    assert t["bytes_per_stored_cell_step"] >= 112.0
