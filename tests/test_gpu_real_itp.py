@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from gpu_cases import harmonic64, ragged_shell, rel_l2, shell
-from paper_2603_05447_gb300 import gpe
+from paper_2603_05447_gb300 import gpe, inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -134,3 +134,40 @@ def test_complex_only_calls_refuse_real_states():
     finally:
         A.close()
         B.close()
+
+
+def test_region_error_shrinks_with_the_cutoff_and_brick_regions_do_better():
+    """Sec. IV's study of the region of interest on a synthetic shell: real
+    FP64 ground states on {V < r mu_TF} against the full-box ground state
+    (same operator and time step).  The error falls with r, and the brick
+    region, a superset of the cell region at the same r, does better."""
+    wl = inputs.SHELL_64
+    b = wl.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    V = inputs.dense_potential(b, wl.potential)
+    mu_tf = gpe.gpe_tf_mu_dense(gb, V, wl.g, wl.N)
+    p = gpe.gpe_imag_params(wl.g, 2.0 / (3 * 2.0 / b.hx ** 2), wl.N)
+    psi0 = np.sqrt(np.maximum(mu_tf - V, 0.0) / wl.g)
+
+    def ground(V_cut, mode):
+        grid = gpe.gpe_grid_create_dense(gb, V, V_cut, gpe.make_opts((8, 8, 8), mode))
+        st = gpe.gpe_state_create(grid, gpe.GPE_R64)
+        try:
+            gpe.gpe_state_load(st, np.ascontiguousarray(psi0), gpe.GPE_LAYOUT_DENSE)
+            gpe.gpe_step_imag(st, p, 4000)
+            gpe.gpe_ground_state(st, p, 1e-11, 100, 400000)
+            out = np.zeros(b.shape)
+            gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_DENSE)
+            return out
+        finally:
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(grid)
+
+    ref = ground(np.inf, gpe.GPE_MASK_CELL)
+    err = {(mode, r): float(np.sum(np.abs(ref ** 2 - ground(r * mu_tf, mode) ** 2)) * b.dV / wl.N)
+           for mode in (gpe.GPE_MASK_CELL, gpe.GPE_MASK_BRICK) for r in (1.5, 3.0)}
+    for mode in (gpe.GPE_MASK_CELL, gpe.GPE_MASK_BRICK):
+        assert err[(mode, 3.0)] < 0.1 * err[(mode, 1.5)]
+    for r in (1.5, 3.0):
+        assert err[(gpe.GPE_MASK_BRICK, r)] < err[(gpe.GPE_MASK_CELL, r)]
+    assert err[(gpe.GPE_MASK_CELL, 3.0)] < 1e-3
