@@ -154,22 +154,43 @@ def oracle_sample(wl, target_s=12.0, layers=48):
     return g, g.compact(V), psi
 
 
-def cpu_baseline(wl, target_s=12.0):
+def _oracle_rk4_rate(oracle, g, V, psi, gg, dt, steps):
+    """Active-cell RK4 steps per second of the FP64 oracle over `steps` steps."""
+    y = oracle.rk4_step(g, V, psi, gg, 0.0, dt)                  # first touch
+    t0 = time.perf_counter()
+    for q in range(steps):
+        y = oracle.rk4_step(g, V, y, gg, (q + 1) * dt, dt)
+    el = time.perf_counter() - t0
+    return {"value": g.n * steps / el, "unit": "cell-steps/s", "steps": steps, "n_active": g.n,
+            "seconds": round(el, 3)}
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle on the host cores: the headline shell (a slab of it, 100
+    RK4 steps), the all-active 64^3 harmonic trap (C1, 100 RK4 steps), and
+    both on a single thread (the paper's CPU figures are single-threaded);
+    cores = the CPUs this process may run on (its affinity mask)."""
     import oracle
+    from paper_2603_05447_gb300 import inputs
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    used = oracle.set_threads(cores)
     g, V, psi = oracle_sample(wl)
     dt = wl.stable_dt()
-    t0 = time.perf_counter()
-    y = oracle.rk4_step(g, V, psi, wl.g, 0.0, dt)
-    one = time.perf_counter() - t0
-    n = max(1, int(target_s / max(one, 1e-3)))
-    t0 = time.perf_counter()
-    for q in range(n):
-        y = oracle.rk4_step(g, V, y, wl.g, (q + 1) * dt, dt)
-    el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": g.n * n / el, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle RK4, {n} steps on a {g.n}-cell slab (48 z-planes through the "
-                      f"equator) of the same shell, {el:.1f} s"}
+    c2 = _oracle_rk4_rate(oracle, g, V, psi, wl.g, dt, 100)
+    box = inputs.cubic_box(64, 0.25)
+    Vd = inputs.dense_potential(box, inputs.Harmonic())
+    g1 = oracle.Grid(np.ones(box.shape, bool), box.hx)
+    psi1 = g1.compact(inputs.gaussian_with_noise(box, seed=1, noise=1e-3))
+    V1 = g1.compact(Vd)
+    c1 = _oracle_rk4_rate(oracle, g1, V1, psi1, 100.0, 1e-3, 100)
+    oracle.set_threads(1)
+    single = {"c1_64cubed": _oracle_rk4_rate(oracle, g1, V1, psi1, 100.0, 1e-3, 100),
+              "c2_slab": _oracle_rk4_rate(oracle, g, V, psi, wl.g, dt, 10)}
+    oracle.set_threads(used)
+    return {"value": c2["value"], "unit": "cell-steps/s", "cores": used, "kind": "oracle",
+            "sample": f"FP64 oracle RK4, 100 steps on a {g.n}-cell slab (48 z-planes through the equator) of "
+                      f"the headline shell, {c2['seconds']} s on {used} threads",
+            "c1_64cubed_all_active": c1, "single_thread": single}
 
 
 # ----------------------------------------------------------------- ranks
@@ -228,22 +249,58 @@ def time_rk4(gpe, torch, st, params, steps, warmup, n_active, g):
     return total, rk / (steps * STEPS_PER_BENCH)
 
 
-# FP64 operations per stored cell and RK4 step of the stage kernels (static
-# V; an FMA counts 2): Laplacian 20 per stage; update 15, 21, 15, 19 for
-# stages 0-3
-FP64_FLOPS_PER_STORED_CELL_STEP = 4 * 20 + 15 + 21 + 15 + 19
+# FP64 operations per cell and RK4 step of the stage kernels (static V; an
+# FMA counts 2): Laplacian 20 per stage; update 15, 21, 15, 19 for stages 0-3.
+# Counted per ACTIVE cell: the inactive cells of stored segments are skipped
+# by the update, and their Laplacian is padding work, not the method's.
+FP64_FLOPS_PER_CELL_STEP = 4 * 20 + 15 + 21 + 15 + 19
+FP32_VS_FP64_STEPS = 10000        # the FP32-vs-FP64 comparison window (RK4 steps)
 
 
-def fp64_roofline(n_stored, rk_ms, clocks):
-    """The complex128 step is bound by GB300's FP64 arithmetic: peak = 152
-    SMs x 2 FP64 FMA per clock x 2 flops x the SM clock (the nominal 1.25
-    TFLOP/s at 2070 MHz)."""
-    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
-    achieved = FP64_FLOPS_PER_STORED_CELL_STEP * n_stored / (rk_ms / 1e3) / 1e12
+def fp64_roofline(gpe, n_active, rk_ms):
+    """The complex128 step is bound by the GPU's FP64 arithmetic: its roof is
+    the FP64 FMA rate measured on this GPU (gpe_fma_peak, CUDA events)."""
+    peak, sec = gpe.gpe_fma_peak(gpe.GPE_F64, 20000)
+    achieved = FP64_FLOPS_PER_CELL_STEP * n_active / (rk_ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "flops_per_stored_cell_step": FP64_FLOPS_PER_STORED_CELL_STEP,
-            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x SM clock"}
+            "flops_per_active_cell_step": FP64_FLOPS_PER_CELL_STEP,
+            "peak_kind": "measured: FP64 FMA chains on every SM, %.2f s, CUDA events (gpe_fma_peak)" % sec}
+
+
+def fp32_vs_fp64(gpe, torch, grid, psi64, params, g, n_stored, checkpoints=(100, 1000, FP32_VS_FP64_STEPS)):
+    """complex64 and complex128 runs from the same (complex64-rounded) input,
+    compared at each checkpoint: relative L2 error of the FP32 state against
+    the FP64 one, and the norm drift |N32 - N64| / N64.  The complex128 run is
+    timed (CUDA events, observables excluded)."""
+    st64 = gpe.gpe_state_create(grid, gpe.GPE_C64)
+    st128 = gpe.gpe_state_create(grid, gpe.GPE_C128)
+    gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
+    gpe.gpe_state_load(st128, np.ascontiguousarray(psi64.astype(np.complex128)), gpe.GPE_LAYOUT_COMPACT)
+    stream = torch.cuda.current_stream()
+    a = np.empty(n_stored, np.complex64)
+    c = np.empty(n_stored, np.complex128)
+    done, ms128, out = 0, 0.0, []
+    for cp in checkpoints:
+        n = cp - done
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        gpe.gpe_step_real(st128, params, n, done * params.dt)
+        e1.record(stream)
+        gpe.gpe_step_real(st64, params, n, done * params.dt)
+        torch.cuda.synchronize()
+        ms128 += e0.elapsed_time(e1)
+        done = cp
+        gpe.gpe_state_store(st64, a, gpe.GPE_LAYOUT_COMPACT)
+        gpe.gpe_state_store(st128, c, gpe.GPE_LAYOUT_COMPACT)
+        o64, o128 = gpe.gpe_observables(st64, g), gpe.gpe_observables(st128, g)
+        out.append({"steps": cp,
+                    "rel_l2": float(np.linalg.norm(a.astype(np.complex128) - c) / np.linalg.norm(c)),
+                    "norm_drift": abs(o64["norm"] - o128["norm"]) / o128["norm"],
+                    "norm_fp32": o64["norm"], "norm_fp64": o128["norm"]})
+    gpe.gpe_state_destroy(st64)
+    gpe.gpe_state_destroy(st128)
+    return out, ms128 / done
 
 
 def time_itp(gpe, torch, st, ip, steps, warmup):
@@ -405,24 +462,12 @@ def _run_ours(args, torch, world, rank, local):
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     e2e_value = n_active * STEPS_PER_BENCH * e2e_steps * world / e2e_s
 
-    # ---- complex128 path and the FP32-vs-FP64 error after the same steps
-    st128 = gpe.gpe_state_create(grid, gpe.GPE_C128)
-    gpe.gpe_state_load(st128, np.ascontiguousarray(psi0), gpe.GPE_LAYOUT_COMPACT)
-    gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
-    n128 = max(1, min(args.steps, 2))
-    t128_ms, rk128_ms = time_rk4(gpe, torch, st128, params, n128, 1, n_active, wl.g)
-    fp64_value = n_active * STEPS_PER_BENCH * n128 * world / (max_over_ranks(world, t128_ms) / 1e3)
-    gpe.gpe_step_real(st64, params, STEPS_PER_BENCH * (n128 + 1))
-    a = np.empty(n_stored, np.complex64)
-    c = np.empty(n_stored, np.complex128)
-    gpe.gpe_state_store(st64, a, gpe.GPE_LAYOUT_COMPACT)
-    gpe.gpe_state_store(st128, c, gpe.GPE_LAYOUT_COMPACT)
-    err = float(np.linalg.norm(a.astype(np.complex128) - c) / np.linalg.norm(c))
-    o64 = gpe.gpe_observables(st64, wl.g)
-    o128 = gpe.gpe_observables(st128, wl.g)
-
+    # ---- complex128 path and the FP32-vs-FP64 error after 10^4 RK4 steps
     gpe.gpe_state_destroy(st64)
-    gpe.gpe_state_destroy(st128)
+    cmp, rk128_ms = fp32_vs_fp64(gpe, torch, grid, psi64, params, wl.g, n_stored)
+    fp64_value = n_active * world / (max_over_ranks(world, rk128_ms) / 1e3)
+    last = cmp[-1]
+
     gpe.gpe_grid_destroy(grid)
 
     if rank != 0:
@@ -450,10 +495,12 @@ def _run_ours(args, torch, world, rank, local):
                      "traffic_gbs": traffic / (rk_ms / 1e3) / 1e9 if traffic else None,
                      "traffic_frac": traffic / (rk_ms / 1e3) / 1e9 / peak if traffic else None},
         "fp64": {"value": fp64_value, "unit": "cell-steps/s", "ms_per_rk4_step": rk128_ms,
-                 "roofline": fp64_roofline(n_stored, rk128_ms, clk.summary()),
-                 "fp32_over_fp64": value / fp64_value,
-                 "rel_l2_fp32_vs_fp64": err, "steps_compared": STEPS_PER_BENCH * (n128 + 1),
-                 "norm_fp32": o64["norm"], "norm_fp64": o128["norm"]},
+                 "roofline": fp64_roofline(gpe, n_active, rk128_ms),
+                 "fp32_over_fp64": (n_active / (rk_ms / 1e3)) / fp64_value,
+                 "rel_l2_fp32_vs_fp64": last["rel_l2"], "norm_drift_fp32_vs_fp64": last["norm_drift"],
+                 "steps_compared": last["steps"], "checkpoints": cmp,
+                 "targets": {"rel_l2": 1e-5, "norm_drift": 1e-6},
+                 "same_input": "both runs start from the complex64-rounded initial state"},
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": n_stored * 8,
                 "d2h_bytes_per_step": n_stored * 8 + 7 * 8},
         "itp": itp,
@@ -475,6 +522,8 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
+    cores = oracle.set_threads(len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                               else (os.cpu_count() or 1))
     wl = shell_workload()
     g, V, psi = oracle_sample(wl)
     dt = wl.stable_dt()
@@ -487,7 +536,6 @@ def run_reference(args):
         y = oracle.rk4_step(g, V, y, wl.g, q * dt, dt)
         times.append(time.perf_counter() - t0)
     el = sum(times)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     value = g.n * args.steps / el
     sample = (f"FP64 oracle RK4 on a {g.n}-cell slab (48 z-planes through the equator) of the "
               f"same shell, one RK4 step per bench step")

@@ -78,6 +78,15 @@ int gpe_last_error(char *buf, size_t n);
  * CUDA graphs at capture time only). */
 int gpe_launch_count(uint64_t *out);
 
+/* Arithmetic roof of this GPU (diagnostics; the paper has no counterpart): the
+ * fused multiply-add throughput of the CUDA cores in FP64 (dtype GPE_F64) or
+ * FP32 (GPE_F32), measured by one launch of independent FMA chains on every
+ * SM (iters x 16 x 8 FMAs per thread, about 1 s for FP64 at iters = 20000)
+ * timed with CUDA events.  *tflops = 2 flops per FMA / elapsed time,
+ * *seconds = that time.  The complex128 step is bound by this FP64 rate, not
+ * by HBM.  GPE_ERR_ARG for iters outside [1, 2^24].  Synchronous. */
+int gpe_fma_peak(int dtype, int iters, double *tflops, double *seconds);
+
 /* ------------------------------------------------------------------ grids */
 /* Cartesian bounding box.  (x0, y0, z0) is the centre of cell (0, 0, 0). */
 typedef struct gpe_box {
@@ -98,9 +107,12 @@ enum { GPE_ORDER_ZMAJOR = 0, GPE_ORDER_MORTON = 1 };
  * touches, which keeps the intermediate stage states in L2 on grids whose
  * skewed window fits there; WAVE2 runs an RK4 step as two such launches of
  * two stages each (stages 0-1, then 2-3), a window of a third of WAVE's
- * (imaginary-time steps have two stages: WAVE2 is WAVE there).  All three
- * give bit-identical results. */
-enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2 };
+ * (imaginary-time steps have two stages: WAVE2 is WAVE there).  FLAT runs the
+ * RK4 stages of gpe_step_real one launch per stage, like STAGED, but with one
+ * thread per stored segment gathering its neighbours directly instead of one
+ * warp per brick staging a shared-memory tile (7-point grids; the other calls
+ * run STAGED on such a grid).  All four give the same arithmetic per cell. */
+enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2, GPE_SCHED_FLAT = 3 };
 
 /* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
  * all three are 0), 8x8x4, 8x4x4.  chunk = bricks per wavefront task
@@ -379,11 +391,13 @@ int gpe_overlap(const gpe_state *a, const gpe_state *b, double out[2],
  * 512 KiB compiled into the library, which every GPU that loads the library
  * keeps until the process exits.  Limit: n <= 268,435,456 (one reduction block
  * per 8192 elements, at most 32768 blocks); larger n returns GPE_ERR_ARG.  The
- * first call on each device looks up that array's device address, so make it
- * before capturing any stream.  All calls share the array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Writes out[0..1] (re, im) on the host;
- * synchronous. */
+ * first call on each device looks up that array's device address (and looks it
+ * up again after the device's CUDA context has been destroyed and made anew,
+ * e.g. by cudaDeviceReset), so make the first call before capturing any
+ * stream.  All calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Writes out[0..1] (re, im) on the host; synchronous: the call waits
+ * on `stream` for its result before it returns. */
 int gpe_overlap_noalloc(const void *a, const void *b, int64_t n, int dtype,
                         double dV, double out[2], gpe_stream stream);
 

@@ -95,6 +95,15 @@ def _load():
         return lib
 
 
+def set_threads(n: int) -> int:
+    """Threads the oracle's OpenMP loops use from the calling thread on
+    (host plumbing for timing, no arithmetic); returns the new maximum."""
+    _load()
+    gomp = ctypes.CDLL("libgomp.so.1")
+    gomp.omp_set_num_threads(int(n))
+    return int(gomp.omp_get_max_threads())
+
+
 def _p64(a):
     return a.ctypes.data_as(_c_f64p) if a is not None else None
 

@@ -1,9 +1,12 @@
 """torch.autograd binding of the ramp gradient.
 
 ``ramp_infidelity(knots, problem)`` returns L = 1 - |<psi_t|psi(T)>|^2 after
-the RK4 ramp with schedule ``knots`` as a differentiable torch scalar; its
-backward pass runs the library's discrete adjoint (gpe_ramp_backward).  The
-knots tensor lives on the host (float64); the states live on the GPU.
+the RK4 ramp with schedule ``knots`` as a differentiable torch scalar.  Both
+the loss and its gradient come from the library: the forward pass runs the
+ramp with a checkpoint tape (gpe_ramp_forward) and the discrete adjoint
+(gpe_ramp_backward), which returns L and dL/dknots together; the backward
+pass hands the stored gradient to autograd.  The knots tensor lives on the
+host (float64); the states live on the GPU.
 """
 from __future__ import annotations
 
@@ -33,16 +36,14 @@ class RampProblem:
         return gpe.real_params(self.g, self.dt, gpe.GPE_V_BLEND, [float(k) for k in knots], self.T_ramp)
 
     def forward(self, knots):
+        """Run the ramp from the start state; returns (loss, gradient) from
+        the library's adjoint."""
         if self.tape is not None:
             gpe.gpe_tape_destroy(self.tape)
             self.tape = None
         gpe.gpe_state_copy(self.state, self.start)
         self.tape = gpe.gpe_ramp_forward(self.state, self.params(knots), self.nsteps, self.t0, self.K)
-        c = gpe.gpe_overlap(self.target, self.state)
-        return 1.0 - abs(c) ** 2
-
-    def backward(self, n_knots):
-        return gpe.gpe_ramp_backward(self.tape, self.target, n_knots)
+        return gpe.gpe_ramp_backward(self.tape, self.target, len(knots))
 
     def close(self):
         if self.tape is not None:
@@ -55,15 +56,13 @@ class RampProblem:
 class _RampInfidelity(torch.autograd.Function):
     @staticmethod
     def forward(ctx, knots, problem):
-        ctx.problem = problem
-        ctx.n = knots.numel()
-        loss = problem.forward(knots.detach().cpu().tolist())
+        loss, grad = problem.forward(knots.detach().cpu().tolist())
+        ctx.grad = torch.tensor(grad, dtype=torch.float64)
         return torch.tensor(loss, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, grad_out):
-        _, grad = ctx.problem.backward(ctx.n)
-        return torch.tensor(grad, dtype=torch.float64) * grad_out, None
+        return ctx.grad * grad_out, None
 
 
 def ramp_infidelity(knots: torch.Tensor, problem: RampProblem) -> torch.Tensor:

@@ -302,6 +302,7 @@ struct gpe_grid {
     gpe::BrickRec *d_rec7 = nullptr;  // [nb*7] record of each brick and of its six face neighbours
     gpe::BrickRec *d_rec19 = nullptr; // [nb*19] ... and of its 12 edge neighbours (19-point grids)
     int stencil = 7;                  // 7 or 19 points
+    uint32_t *d_segtab = nullptr;     // [n_packed/4] brick << 7 | local segment (FLAT schedule, built on first use)
     int32_t *d_bvol = nullptr;  // brick-grid volume nbx*nby*nbz -> brick id or -1
     double *d_V[2] = {nullptr, nullptr};
     float *d_Vf[2] = {nullptr, nullptr};  // float copies, made on first use

@@ -30,10 +30,52 @@ struct NoallocScratch {
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;  // 512 KiB + 24 B
 
-// Device address of the scratch array on each device, looked up once per
-// device (in host code the symbol name is only a stand-in for it).
+// Device address of the scratch array, looked up per device and per CUDA
+// context (in host code the symbol name is only a stand-in for it).  The
+// array lives in the library's module, which is loaded into each context: if
+// a device's context is destroyed and made again (cudaDeviceReset, or a
+// framework tearing its context down), the array gets a new address, so the
+// cache is keyed on the context's process-unique id and the lookup repeats
+// when it changes.
+typedef int (*ctx_get_current_fn)(void **ctx);
+typedef int (*ctx_get_id_fn)(void *ctx, unsigned long long *id);
+
+struct NoallocSlot {
+    unsigned long long ctx_id;
+    NoallocScratch *ptr;
+};
+
 static std::mutex g_noalloc_mu;
-static NoallocScratch *g_noalloc_ptr[64] = {nullptr};
+static NoallocSlot g_noalloc_slot[64] = {};
+static ctx_get_current_fn g_ctx_current = nullptr;
+static ctx_get_id_fn g_ctx_id = nullptr;
+
+// id of the calling thread's current context
+static int current_ctx_id(unsigned long long *id)
+{
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        GPE_TRY_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        GPE_TRY_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return fail(GPE_ERR_CUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId not available");
+        g_ctx_current = reinterpret_cast<ctx_get_current_fn>(f1);
+        g_ctx_id = reinterpret_cast<ctx_get_id_fn>(f2);
+    }
+    void *ctx = nullptr;
+    if (g_ctx_current(&ctx) != 0) return fail(GPE_ERR_CUDA, "cuCtxGetCurrent failed");
+    if (!ctx) {
+        // nothing current on this thread yet: cudaSetDevice initialises the
+        // device's primary context and makes it current
+        int dev = 0;
+        GPE_TRY_CUDA(cudaGetDevice(&dev));
+        GPE_TRY_CUDA(cudaSetDevice(dev));
+        if (g_ctx_current(&ctx) != 0 || !ctx) return fail(GPE_ERR_CUDA, "no current CUDA context");
+    }
+    if (g_ctx_id(ctx, id) != 0) return fail(GPE_ERR_CUDA, "cuCtxGetId failed");
+    return GPE_OK;
+}
 
 static int noalloc_scratch(NoallocScratch **out)
 {
@@ -41,17 +83,23 @@ static int noalloc_scratch(NoallocScratch **out)
     GPE_TRY_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(GPE_ERR_STATE, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    unsigned long long id = 0;
+    GPE_TRY(current_ctx_id(&id));
+    NoallocSlot &sl = g_noalloc_slot[dev];
+    if (!sl.ptr || sl.ctx_id != id) {
         void *p = nullptr;
         GPE_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_ptr[dev] = static_cast<NoallocScratch *>(p);
+        sl.ptr = static_cast<NoallocScratch *>(p);
+        sl.ctx_id = id;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = sl.ptr;
     return GPE_OK;
 }
 
 // One block per NOALLOC_CHUNK consecutive elements; partial sums of
-// conj(a) b in FP64, then the last block adds them in block order.
+// conj(a) b in FP64, then the last block to finish adds the per-block partials
+// in a fixed order (strided per thread, then a warp and block tree), so the
+// result is the same from run to run.
 template <typename CT>
 __global__ void __launch_bounds__(NOALLOC_THREADS)
     k_overlap_noalloc(const CT *a, const CT *b, int64_t n, double dV, NoallocScratch *scr)

@@ -28,6 +28,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "flat.cuh"
 #include "gpe_internal.cuh"
 #include "kernels.cuh"
 
@@ -692,6 +693,39 @@ static int replay_graph(gpe_state *st, int which, uint64_t key, int nodes, int64
 
 __global__ void k_add_scalar(double *p, double v) { *p += v; }
 
+// ------------------------------------------------------------ segment table (FLAT schedule)
+// segtab[k] = brick << 7 | q for the k-th stored segment of the packed run
+// (brick b's stored segments start at rec[b].off / 4, in increasing q)
+__global__ void k_segtab(const BrickRec *rec, int64_t nb, int nseg_brick, uint32_t *segtab)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const BrickRec r = rec[b];
+    uint32_t k = r.off / 4u;
+    for (int q = 0; q < nseg_brick; ++q)
+        if ((r.m[q >> 5] >> (q & 31)) & 1u) segtab[k++] = ((uint32_t)b << 7) | (uint32_t)q;
+}
+
+static int ensure_segtab(gpe_grid *g)
+{
+    if (g->d_segtab) return GPE_OK;
+    if (g->nb >= (1LL << 25)) return fail(GPE_ERR_ARG, "too many bricks (%lld) for the FLAT schedule", (long long)g->nb);
+    uint32_t *t = nullptr;
+    GPE_TRY(dev_alloc_t(&t, (size_t)std::max<int64_t>(1, g->n_packed / 4)));
+    if (g->nb > 0) {
+        k_segtab<<<(unsigned)((g->nb + 255) / 256), 256, 0, cudaStreamLegacy>>>(g->d_rec, g->nb, g->bc / 4, t);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
+        count_launch();
+        if (e != cudaSuccess) {
+            dev_free(t);
+            return cuda_fail(e, "k_segtab", __FILE__, __LINE__);
+        }
+    }
+    g->d_segtab = t;
+    return GPE_OK;
+}
+
 // ------------------------------------------------------------ step drivers
 template <typename R, int BX, int BY, int BZ>
 static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, double t0, cudaStream_t s)
@@ -754,6 +788,43 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
             }
         }
         return GPE_OK;
+    }
+    if (g->sched == GPE_SCHED_FLAT) {
+        GPE_TRY(ensure_segtab(const_cast<gpe_grid *>(g)));
+        const FlatView F{g->d_segtab, g->d_rec7, g->n_packed / 4};
+        using RF = Rk4Flat<R, BX, BY, BZ>;
+        typename RF::K kf[4];
+        for (int stg = 0; stg < 4; ++stg) kf[stg] = RF::get(blend, stg);
+        const unsigned nbf = (unsigned)std::max<int64_t>(1, (F.nseg + RF::THREADS - 1) / RF::THREADS);
+        auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
+            for (int64_t n = 0; n < cnt; ++n) {
+                a.t_off = (double)n * p->dt;
+                for (int stg = 0; stg < 4; ++stg) {
+                    kf[stg]<<<nbf, RF::THREADS, 0, cs>>>(a, F);
+                    GPE_LAUNCH_CHECK();
+                }
+            }
+            return GPE_OK;
+        };
+        int64_t left = nsteps;
+        if (use_graph(st, s, nsteps)) {
+            const int G_ = st->graph_steps;
+            uint64_t key = fnv1a(p, sizeof *p);
+            const void *ptrs[2] = {a.V0, a.V1};
+            key = fnv1a(ptrs, sizeof ptrs, key);
+            key = fnv1a(&G_, sizeof G_, key);
+            auto rec_block = [&](cudaStream_t cs) -> int {
+                GPE_TRY(record(cs, G_));
+                if (blend) {
+                    k_add_scalar<<<1, 1, 0, cs>>>(st->d_clock, (double)G_ * p->dt);
+                    GPE_LAUNCH_CHECK();
+                }
+                return GPE_OK;
+            };
+            GPE_TRY(replay_graph(st, 0, key, 4 * G_ + (blend ? 1 : 0), nsteps / G_, s, rec_block));
+            left = nsteps % G_;
+        }
+        return record(s, left);
     }
     using RS = Rk4Stages<R, BX, BY, BZ>;
     typename RS::K k[4];

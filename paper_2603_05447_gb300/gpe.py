@@ -130,6 +130,7 @@ _SIGS = {
     "gpe_version": (C.c_int, []),
     "gpe_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
     "gpe_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "gpe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gpe_grid_create_dense": (C.c_int, [C.POINTER(gpe_box), _P, C.c_int, C.c_int, C.c_double,
                                         C.POINTER(gpe_grid_opts), C.POINTER(_P), _P]),
     "gpe_grid_create_analytic": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.c_double,
@@ -342,6 +343,14 @@ def gpe_launch_count() -> int:
     n = C.c_uint64()
     _check(load().gpe_launch_count(C.byref(n)))
     return n.value
+
+
+def gpe_fma_peak(dtype, iters):
+    """Measured CUDA-core FMA throughput (TFLOP/s, seconds) in FP64 (GPE_F64)
+    or FP32 (GPE_F32)."""
+    t, sec = C.c_double(), C.c_double()
+    _check(load().gpe_fma_peak(int(dtype), int(iters), C.byref(t), C.byref(sec)))
+    return t.value, sec.value
 
 
 def gpe_grid_create_dense(box, V, V_cut, opts=None, stream=None):

@@ -272,6 +272,8 @@ RAMP_2048 = RampWorkload(ShellWorkload(n=2048, a_cells=800.0, g=5000.0), core_ra
 RAMP_512 = RampWorkload(ShellWorkload(n=512, a_cells=200.0, g=5000.0), core_radius=0.24)
 # 48^3 version for parity tests
 RAMP_48 = RampWorkload(ShellWorkload(n=48, a_cells=19.0, g=5000.0), core_radius=0.24)
+# 64^3 version of the adjoint workload, small enough for the FP64 oracle adjoint
+RAMP_64 = RampWorkload(ShellWorkload(n=64, a_cells=24.0, g=5000.0), core_radius=0.24)
 
 
 def stage_fractions(n_stages: int = 66) -> np.ndarray:

@@ -5,6 +5,11 @@ with the FP64 oracle run on the 11^3 patch around each sample.  One RK4 step
 applies the stencil four times, so a cell's new value depends only on cells
 within 4 of it and the patch (half-width 5) reproduces it exactly.
 
+The oracle is fed the potential evaluated on the host in FP64 from the
+workload's formula (not the potential the device builder produced), and every
+sampled patch also checks the builder: the region of interest equals
+{V_host < V_cut} cell by cell and the stored potential equals V_host.
+
 Tolerances as in test_gpu_parity: complex128 1e-12, complex64 2e-6, relative
 to the largest |psi| of the patch.  The imaginary-time step renormalises
 globally; the samples are compared up to one common factor, which must be the
@@ -22,7 +27,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 HALF = 5
-NSAMPLE = 40
+NSAMPLE = 300
 
 
 @pytest.fixture(scope="module")
@@ -45,29 +50,45 @@ def big():
     off = 4 * np.concatenate([[0], np.cumsum(seg.sum(axis=1))[:-1]]).astype(np.int64)
     rank = np.cumsum(seg, axis=1) - 1
     shape = np.array([info.bx, info.by, info.bz])
-    bid = {tuple(c): n for n, c in enumerate(org // shape)}
-    yield dict(wl=wl, grid=grid, psi0=psi0, info=info, act=act, seg=seg, off=off, rank=rank, bid=bid, V=V,
+    nbx, nby, nbz = (-(-wl.box.nx // shape[0]), -(-wl.box.ny // shape[1]), -(-wl.box.nz // shape[2]))
+    bvol = -np.ones((nbz, nby, nbx), np.int64)
+    bo = org // shape
+    bvol[bo[:, 2], bo[:, 1], bo[:, 0]] = np.arange(info.n_bricks)
+    yield dict(wl=wl, grid=grid, psi0=psi0, info=info, act=act, seg=seg, off=off, rank=rank, bvol=bvol, V=V,
                shape=tuple(int(x) for x in shape))
     gpe.gpe_grid_destroy(grid)
 
 
 def patch(B, i, j, k):
-    """Mask, packed indices (-1 = not active) of the (2H+1)^3 patch at (i, j, k)."""
+    """Mask, packed indices (-1 = not active) and host FP64 potential of the
+    (2H+1)^3 patch at (i, j, k); also checks the builder on the patch: the
+    active cells are exactly those with V_host < V_cut, and the stored
+    potential equals V_host there."""
+    wl = B["wl"]
+    b_ = wl.box
     r = np.arange(-HALF, HALF + 1)
     K, J, I = np.meshgrid(k + r, j + r, i + r, indexing="ij")
-    n = B["wl"].box.nx
+    inside = (I >= 0) & (I < b_.nx) & (J >= 0) & (J < b_.ny) & (K >= 0) & (K < b_.nz)
+    bx, by, bz = B["shape"]
     idx = -np.ones(K.shape, np.int64)
-    inside = (I >= 0) & (I < n) & (J >= 0) & (J < n) & (K >= 0) & (K < n)
-    for (a, b_, c) in zip(*np.nonzero(inside)):
-        ii, jj, kk = I[a, b_, c], J[a, b_, c], K[a, b_, c]
-        bx, by, bz = B["shape"]
-        b = B["bid"].get((ii // bx, jj // by, kk // bz))
-        if b is None:
-            continue
-        l = (ii % bx) + bx * ((jj % by) + by * (kk % bz))
-        if B["act"][b, l]:
-            idx[a, b_, c] = B["off"][b] + 4 * B["rank"][b, l // 4] + l % 4
-    return idx >= 0, idx
+    Ii, Ji, Ki = I[inside], J[inside], K[inside]
+    bid = B["bvol"][Ki // bz, Ji // by, Ii // bx]
+    l = (Ii % bx) + bx * ((Ji % by) + by * (Ki % bz))
+    has = bid >= 0
+    act = np.zeros(Ii.shape, bool)
+    act[has] = B["act"][bid[has], l[has]]
+    sub = np.full(Ii.shape, -1, np.int64)
+    sub[act] = B["off"][bid[act]] + 4 * B["rank"][bid[act], l[act] // 4] + l[act] % 4
+    idx[inside] = sub
+    Vh = np.full(K.shape, np.inf)
+    Vh[inside] = wl.potential(b_.x0 + Ii * b_.hx, b_.y0 + Ji * b_.hy, b_.z0 + Ki * b_.hz)
+    m = idx >= 0
+    # the builder's region and potential against the host evaluation (cells
+    # within 1e-12 of the cutoff may round either way)
+    clear = np.abs(Vh - wl.V_cut) > 1e-12 * wl.V_cut
+    assert np.array_equal(m[inside & clear], (Vh < wl.V_cut)[inside & clear]), (i, j, k)
+    assert np.all(np.abs(B["V"][idx[m]] - Vh[m]) <= 1e-12 * wl.V_cut), (i, j, k)
+    return m, idx, Vh
 
 
 def samples(B, seed):
@@ -110,9 +131,9 @@ def test_rk4_full_size_sampled(big, dtype, tol):
     before, after = run(big, dtype, "rk4")
     wl = big["wl"]
     for (i, j, k) in samples(big, 11):
-        m, idx = patch(big, i, j, k)
+        m, idx, Vh = patch(big, i, j, k)
         g = oracle.Grid(m, wl.box.hx)
-        y = oracle.rk4_step(g, big["V"][idx[m]], before[idx[m]], wl.g, 0.0, wl.stable_dt())
+        y = oracle.rk4_step(g, Vh[m], before[idx[m]], wl.g, 0.0, wl.stable_dt())
         c = np.flatnonzero(np.all(g.ijk() == HALF, axis=1))[0]
         ref = y[c]
         got = after[idx[HALF, HALF, HALF]]
@@ -126,10 +147,10 @@ def test_itp_full_size_sampled_up_to_one_factor(big, dtype, tol):
     wl = big["wl"]
     got, ref, scl = [], [], []
     for (i, j, k) in samples(big, 12):
-        m, idx = patch(big, i, j, k)
+        m, idx, Vh = patch(big, i, j, k)
         g = oracle.Grid(m, wl.box.hx)
         # the step before its renormalisation: N chosen so the factor is 1
-        y, nrm = oracle.itp_step(g, big["V"][idx[m]], before[idx[m]], wl.g, wl.stable_dt(), 1.0)
+        y, nrm = oracle.itp_step(g, Vh[m], before[idx[m]], wl.g, wl.stable_dt(), 1.0)
         y = y / math.sqrt(1.0 / nrm)
         c = np.flatnonzero(np.all(g.ijk() == HALF, axis=1))[0]
         ref.append(y[c])
@@ -168,9 +189,9 @@ def test_rk4_19_point_full_size_sampled(big):
         gpe.gpe_grid_destroy(grid)
     before, after = before.astype(np.complex128), after.astype(np.complex128)
     for (i, j, k) in samples(big, 13):
-        m, idx = patch(big, i, j, k)
+        m, idx, Vh = patch(big, i, j, k)
         g = oracle.Grid(m, wl.box.hx)
-        y = oracle.rk_step_np(g, big["V"][idx[m]], before[idx[m]], wl.g, 0.0, wl.stable_dt(), "RK4", stencil=19)
+        y = oracle.rk_step_np(g, Vh[m], before[idx[m]], wl.g, 0.0, wl.stable_dt(), "RK4", stencil=19)
         c = np.flatnonzero(np.all(g.ijk() == HALF, axis=1))[0]
         scale = np.max(np.abs(before[idx[m]]))
         assert abs(after[idx[HALF, HALF, HALF]] - y[c]) <= tol * scale, (i, j, k)
