@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 STEPS_PER_BENCH = 100
+FLOOR_CHECKS = 10                 # batch workload: checks that measure the complex64 |dmu| floor
 B_ALG = {"c64": 20.0, "c128": 40.0}   # algorithmic bytes per active cell-step (read psi, V; write psi)
 METRIC = "shell-grid GPE cell-steps/s: FP32 vs FP64 at stated error; % of HBM roofline"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rk4_shell1024_c64_traffic.json")
@@ -104,7 +105,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- workload
 WORKLOADS = {"shell1024": "SHELL_1024", "shell512": "SHELL_512"}
-EXTRA = ("ramp2048", "adjoint512", "batch", "roi_sweep", "stages512")
+EXTRA = ("ramp2048", "adjoint512", "batch", "roi_sweep", "stages512", "ramp_traced")
 _workload_name = "shell1024"
 
 
@@ -481,7 +482,7 @@ def _run_ours(args, torch, world, rank, local):
                                "g=2000, N=1, mask V<5mu0, RK4 real time, complex64 bulk + FP64 reductions",
                    "n_active": n_active, "n_packed": n_stored, "brick": f"{info.bx}x{info.by}x{info.bz}",
                    "grid_build_s": round(t_build, 4),
-                   "schedule": "staged" if args.sched == 0 else "wavefront",
+                   "schedule": {0: "staged", 1: "wavefront", 2: "wavefront (stage pairs)", 3: "fused stage pairs"}[args.sched],
                    "rk4_steps_per_bench_step": STEPS_PER_BENCH, "dt": dt,
                    "l2": "inputs larger than L2 (state %.0f MB + potential %.0f MB)" % (n_stored * 8 / 1e6, n_stored * 4 / 1e6),
                    "parallelism": f"replicas x{world}"},
@@ -489,7 +490,8 @@ def _run_ours(args, torch, world, rank, local):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": {0: "RK4 step (k_rk4_staged, four launches per step)",
                                 1: "RK4 step (k_rk4_wave, one launch per step)",
-                                2: "RK4 step (k_rk4_wave, two launches of two stages per step)"}[args.sched],
+                                2: "RK4 step (k_rk4_wave, two launches of two stages per step)",
+                                3: "RK4 step (k_rk4_pair2, two launches of two fused stages per step)"}[args.sched],
                      "peak_kind": peak_kind,
                      "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms,
                      "traffic_gbs": traffic / (rk_ms / 1e3) / 1e9 if traffic else None,
@@ -684,6 +686,96 @@ def roi_sweep(gpe, inputs, torch):
                       "8^3 bricks; brick mode keeps every cell of a brick holding a selected cell"}
 
 
+def ramp_traced(gpe, inputs, torch, nsteps=5000, every=500, n_overlap=5, nsteps_overlap=4000):
+    """The hollowing ramp of the 2048^3 box tracked over a run of `nsteps` RK4
+    steps (the configuration names 5e4; a tenth is run): norm and energy
+    every `every` steps through gpe_step_real_traced.  The overlap with the
+    instantaneous ground state needs a ground-state solve of V(s(t)) per
+    trace point, so it is tracked on the 512^3 version of the same ramp:
+    at n_overlap points of an `nsteps_overlap`-step run, the ground state of
+    (1 - s) V0 + s V1 (complex64, Thomas-Fermi start, region V < 5 mu_TF) is
+    solved and |<psi_gs | psi(t)>|^2 taken after remapping psi(t) onto its
+    grid (cells of psi(t) outside that region are dropped)."""
+    out = {}
+    knots = inputs.monotone_knots(16, seed=3)
+    # 2048^3: traced norm and energy
+    rw = inputs.RAMP_2048
+    grid = _ramp_grid(gpe, rw)
+    info = gpe.gpe_grid_get_info(grid)
+    st = gpe.gpe_state_create(grid, gpe.GPE_C64)
+    gpe.gpe_state_load(st, _core_state(gpe, inputs, rw, grid, gpe.GPE_C64), gpe.GPE_LAYOUT_COMPACT)
+    dt = 0.2 / (6.0 / rw.shell.h ** 2 + info.v_max)
+    p = gpe.real_params(rw.shell.g, dt, gpe.GPE_V_BLEND, knots, nsteps * dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trace = gpe.gpe_step_real_traced(st, p, nsteps, every)
+    el = time.perf_counter() - t0
+    out["box2048"] = {"n_active": info.n_active, "steps": nsteps, "every": every, "dt": dt, "seconds": el,
+                      "cell_steps_per_s": info.n_active * nsteps / el,
+                      "trace": [{"step": (k + 1) * every, "norm": o["norm"], "energy": o["energy"], "mu": o["mu"]}
+                                for k, o in enumerate(trace)]}
+    gpe.gpe_state_destroy(st)
+    gpe.gpe_grid_destroy(grid)
+    # 512^3: overlap with the instantaneous ground state
+    rw = inputs.RAMP_512
+    b = rw.shell.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    grid = _ramp_grid(gpe, rw)
+    info = gpe.gpe_grid_get_info(grid)
+    st = gpe.gpe_state_create(grid, gpe.GPE_C64)
+    gpe.gpe_state_load(st, _core_state(gpe, inputs, rw, grid, gpe.GPE_C64), gpe.GPE_LAYOUT_COMPACT)
+    dt = 0.2 / (6.0 / rw.shell.h ** 2 + info.v_max)
+    T = nsteps_overlap * dt
+    p = gpe.real_params(rw.shell.g, dt, gpe.GPE_V_BLEND, knots, T)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    V0 = torch.empty((b.nz, b.ny, b.nx), dtype=torch.float64, device=dev)
+    V1 = torch.empty_like(V0)
+    x, y, z = b.axes()
+    for k0 in range(0, b.nz, 32):
+        Z, Y, X = np.meshgrid(z[k0:k0 + 32], y, x, indexing="ij")
+        V0[k0:k0 + 32].copy_(torch.from_numpy(rw.v0(X, Y, Z)))
+        V1[k0:k0 + 32].copy_(torch.from_numpy(rw.shell.potential(X, Y, Z)))
+    tknots = np.linspace(0.0, T, len(knots))
+    points, done = [], 0
+    marks = [int(round(q * nsteps_overlap / (n_overlap - 1))) for q in range(n_overlap)]
+    for m in marks:
+        if m > done:
+            gpe.gpe_step_real(st, p, m - done, done * dt)
+            done = m
+        s_t = float(np.interp(done * dt, tknots, knots))
+        Vs = ((1.0 - s_t) * V0 + s_t * V1).contiguous()
+        mu = gpe.gpe_tf_mu_dense(gb, Vs, rw.shell.g, rw.shell.N)
+        g2 = gpe.gpe_grid_create_dense(gb, Vs, 5.0 * mu, gpe.make_opts((8, 8, 4)))
+        gs = gpe.gpe_state_create(g2, gpe.GPE_C64)
+        gpe.gpe_state_load(gs, torch.sqrt(torch.clamp(mu - Vs, min=0.0) / rw.shell.g).to(torch.complex64).contiguous(),
+                           gpe.GPE_LAYOUT_DENSE)
+        dti = min(0.5 * rw.shell.h ** 2, 0.5 / mu)
+        try:
+            n_gs, ogs = gpe.gpe_ground_state(gs, gpe.gpe_imag_params(rw.shell.g, dti, rw.shell.N), 1e-7 * mu, 100,
+                                             20000)
+            conv = True
+        except gpe.GpeError:
+            n_gs, ogs, conv = 20000, gpe.gpe_observables(gs, rw.shell.g), False
+        tmp = gpe.gpe_state_create(g2, gpe.GPE_C64)
+        gpe.gpe_state_remap(tmp, st)
+        c = gpe.gpe_overlap(gs, tmp)
+        o_t = gpe.gpe_observables(st, rw.shell.g, s_t)
+        points.append({"step": done, "s": s_t, "fidelity": abs(c) ** 2, "norm": o_t["norm"],
+                       "energy": o_t["energy"], "mu_ground": ogs["mu"], "ground_steps": n_gs,
+                       "ground_converged": conv, "n_active_ground": gpe.gpe_grid_get_info(g2).n_active})
+        for h_ in (tmp, gs):
+            gpe.gpe_state_destroy(h_)
+        gpe.gpe_grid_destroy(g2)
+        del Vs
+    out["box512_overlap"] = {"n_active": info.n_active, "steps": nsteps_overlap, "dt": dt, "points": points}
+    gpe.gpe_state_destroy(st)
+    gpe.gpe_grid_destroy(grid)
+    return {"metric": "hollowing ramp tracked: norm, energy (2048^3) and overlap with the instantaneous ground "
+                      "state (512^3)", "unit": "various", **out,
+            "config": "ramp workload (harmonic core -> thin shell, g=5000, 16 seeded monotone knots over the run), "
+                      "complex64 RK4; the configuration's 5e4 steps cut to the step counts stated"}
+
+
 def run_extra(args):
     """Ramp (2048^3, ~1e8 active), adjoint (512^3) and batch workloads: one
     JSON line each, beside the headline line of the default run."""
@@ -704,6 +796,8 @@ def run_extra(args):
             line.update(roi_sweep(gpe, inputs, torch))
         elif args.workload == "stages512":
             line.update(stages_run(gpe, inputs, torch))
+        elif args.workload == "ramp_traced":
+            line.update(ramp_traced(gpe, inputs, torch))
         elif args.workload in ("ramp2048", "adjoint512"):
             rw = inputs.RAMP_2048 if args.workload == "ramp2048" else inputs.RAMP_512
             grid = _ramp_grid(gpe, rw)
@@ -807,9 +901,26 @@ def run_extra(args):
                                                               args.steps * STEPS_PER_BENCH, check=False)
             el = gdist.max_over_ranks(time.perf_counter() - t0)
             done = gdist.sum_over_ranks(sum(cells[i] * s for i, s in zip(mine, steps)))
+            # the complex64 floor: per shell, |dmu| between FLOOR_CHECKS further
+            # checks of 100 steps each (outside the timed region)
+            floors = []
+            for k, i in enumerate(mine):
+                mus = []
+                for _ in range(FLOOR_CHECKS + 1):
+                    gpe.gpe_step_imag(states[k], params[k], 100)
+                    mus.append(gpe.gpe_observables(states[k], shells[i].g)["mu"])
+                d = np.abs(np.diff(mus))
+                floors.append({"shell": i, "n_active": cells[i], "converged": bool(conv[k]), "steps": int(steps[k]),
+                               "mu": mus[-1], "dmu_median": float(np.median(d)), "dmu_max": float(np.max(d)),
+                               "dmu_median_rel": float(np.median(d) / abs(mus[-1]))})
+            med = np.array([f["dmu_median"] for f in floors])
             line.update(metric="batched ground states: active-cell ITP steps/s (complex64, FP64 norms)",
                         unit="cell-steps/s", value=done / el, shells=len(shells), n_active_total=int(sum(cells)),
                         converged=int(gdist.sum_over_ranks(sum(conv))), tol_dmu=args.tol,
+                        floor={"checks": FLOOR_CHECKS, "every": 100,
+                               "below_tol": int(np.sum(med < args.tol)),
+                               "dmu_median_quantiles": [float(np.quantile(med, q)) for q in (0, 0.5, 0.9, 1)],
+                               "per_shell": floors},
                         max_steps=args.steps * STEPS_PER_BENCH, seconds=el, scaling="strong",
                         config="seeded uneven ellipsoidal shells (radius U[0.5,1] x 360 cells, aspects U[0.7,1], "
                                "thickness U[4,10] cells, g U[100,3000]), one persistent launch, graph-replayed, "
@@ -837,7 +948,8 @@ def main():
     ap.add_argument("--integrators", action="store_true", help="a --quick run also times RKHE3 and RKCK")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident complex64 timing only (for profiling runs)")
-    ap.add_argument("--sched", type=int, default=0, help="0 staged (default), 1 wavefront, 2 two-stage wavefront")
+    ap.add_argument("--sched", type=int, default=0,
+                    help="0 staged, 1 wavefront, 2 two-stage wavefront, 3 fused stage pairs")
     ap.add_argument("--chunk", type=int, default=0, help="bricks per wavefront task (0: default)")
     ap.add_argument("--brick", type=int, nargs=3, default=[8, 8, 4])
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64", help="state type of a --quick run")

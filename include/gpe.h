@@ -107,12 +107,13 @@ enum { GPE_ORDER_ZMAJOR = 0, GPE_ORDER_MORTON = 1 };
  * touches, which keeps the intermediate stage states in L2 on grids whose
  * skewed window fits there; WAVE2 runs an RK4 step as two such launches of
  * two stages each (stages 0-1, then 2-3), a window of a third of WAVE's
- * (imaginary-time steps have two stages: WAVE2 is WAVE there).  FLAT runs the
- * RK4 stages of gpe_step_real one launch per stage, like STAGED, but with one
- * thread per stored segment gathering its neighbours directly instead of one
- * warp per brick staging a shared-memory tile (7-point grids; the other calls
- * run STAGED on such a grid).  All four give the same arithmetic per cell. */
-enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2, GPE_SCHED_FLAT = 3 };
+ * (imaginary-time steps have two stages: WAVE2 is WAVE there).  PAIR runs
+ * the RK4 step of gpe_step_real as two launches, stages 0+1 and stages 2+3,
+ * each brick recomputing the first stage of a pair on its one-cell face halo
+ * so that the middle stage never leaves shared memory (64 instead of 112
+ * bytes of compulsory traffic per stored cell in complex64); the other calls
+ * run STAGED on such a grid.  All four give bit-identical results. */
+enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2, GPE_SCHED_PAIR = 3 };
 
 /* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
  * all three are 0), 8x8x4, 8x4x4.  chunk = bricks per wavefront task

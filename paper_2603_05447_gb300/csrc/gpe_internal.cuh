@@ -287,6 +287,12 @@ void red_free(RedScratch &r);
 }  // namespace gpe
 
 // ------------------------------------------------------------ handles
+// launch the staged stage kernels with programmatic dependent launch (off:
+// measured no gain for RK4 and a slower imaginary-time step on GB300)
+#ifndef GPE_PDL
+#define GPE_PDL 0
+#endif
+
 struct gpe_grid {
     int device = 0;
     gpe_box box{};
@@ -302,7 +308,7 @@ struct gpe_grid {
     gpe::BrickRec *d_rec7 = nullptr;  // [nb*7] record of each brick and of its six face neighbours
     gpe::BrickRec *d_rec19 = nullptr; // [nb*19] ... and of its 12 edge neighbours (19-point grids)
     int stencil = 7;                  // 7 or 19 points
-    uint32_t *d_segtab = nullptr;     // [n_packed/4] brick << 7 | local segment (FLAT schedule, built on first use)
+    int32_t *d_nbr18 = nullptr;       // [nb*18] face then edge neighbour ids (PAIR schedule, built on first use)
     int32_t *d_bvol = nullptr;  // brick-grid volume nbx*nby*nbz -> brick id or -1
     double *d_V[2] = {nullptr, nullptr};
     float *d_Vf[2] = {nullptr, nullptr};  // float copies, made on first use
@@ -345,6 +351,7 @@ struct gpe_state {
     unsigned long long ticket_base = 0, finish_base = 0;
     // CUDA graphs of `graph_steps` staged steps ([0] real time, [1] imaginary)
     int graph_steps = 32;
+    bool pdl = GPE_PDL != 0;  // stage kernels launched with programmatic dependent launch
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     unsigned long long gkey[2] = {0, 0};
     int gnodes[2] = {0, 0};

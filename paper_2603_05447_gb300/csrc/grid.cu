@@ -483,7 +483,7 @@ static void grid_free(gpe_grid *g)
     dev_free(g->d_rec);
     dev_free(g->d_rec7);
     dev_free(g->d_rec19);
-    dev_free(g->d_segtab);
+    dev_free(g->d_nbr18);
     dev_free(g->d_chunk_lohi);
     dev_free(g->d_tasks);
     dev_free(g->d_dep_off);
@@ -517,7 +517,7 @@ static int build_grid(const gpe_box *box, const VSource &src, const gpe_grid_opt
         return fail(GPE_ERR_ARG, "unknown brick order %d", o.order);
     if (o.stencil != 0 && o.stencil != 7 && o.stencil != 19) return fail(GPE_ERR_ARG, "stencil must be 7 or 19");
     if (o.sched != GPE_SCHED_WAVE && o.sched != GPE_SCHED_WAVE2 && o.sched != GPE_SCHED_STAGED &&
-        o.sched != GPE_SCHED_FLAT)
+        o.sched != GPE_SCHED_PAIR)
         return fail(GPE_ERR_ARG, "unknown schedule %d", o.sched);
     if (o.chunk < 0 || o.chunk > 4096) return fail(GPE_ERR_ARG, "chunk must be in [0, 4096]");
 

@@ -96,6 +96,7 @@ __device__ __forceinline__ void itp_brick_b(const ItpArgs<R, CT> &a, const GridV
 template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T, int NP = 7>
 __global__ void GPE_BOUNDS_NP(R) k_itp_a(const ItpArgs<R, CT> a, const GridView G)
 {
+    pdl_enter();
     constexpr int NW = KernelCfg<R>::NW;
     auto &ws = warp_space<R, BX, BY, BZ, CT, NP>();
     const int warp = threadIdx.x >> 5;
@@ -109,6 +110,7 @@ template <typename R, int BX, int BY, int BZ, typename CT = typename Cx<R>::T, i
 __global__ void GPE_BOUNDS_NP(R) k_itp_b(const ItpArgs<R, CT> a, const GridView G, double *partials,
                                           unsigned int *counter)
 {
+    pdl_enter();
     constexpr int NW = KernelCfg<R>::NW;
     auto &ws = warp_space<R, BX, BY, BZ, CT, NP>();
     const int warp = threadIdx.x >> 5;

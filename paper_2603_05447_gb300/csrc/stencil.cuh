@@ -91,6 +91,50 @@ struct RealOf<double2> {
     using T = double;
 };
 
+// Packed single-precision pairs: the f32x2 add / multiply / fused
+// multiply-add instructions of sm_100 and later act on both halves of a
+// 64-bit register pair, i.e. on the real and imaginary parts of a complex64
+// value at once, each half rounded exactly as the scalar instruction would
+// round it.  They halve the arithmetic instruction count of the complex64
+// stencils without changing any result.
+__device__ __forceinline__ unsigned long long f2pk(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2up(unsigned long long r)
+{
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pk(a)), "l"(f2pk(b)));
+    return f2up(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)  // a - b
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pk(a)), "l"(f2pk(b)));
+    return f2up(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pk(a)), "l"(f2pk(b)));
+    return f2up(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)  // a * b + c, one rounding per half
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2pk(a)), "l"(f2pk(b)), "l"(f2pk(c)));
+    return f2up(d);
+}
+__device__ __forceinline__ float2 dup2(float f) { return make_float2(f, f); }
+
 template <typename CT>
 __device__ __forceinline__ CT czero()
 {
@@ -113,6 +157,7 @@ __device__ __forceinline__ typename RealOf<CT>::T norm2(const CT &v)
         return v * v;
 }
 // v * f, f real
+__device__ __forceinline__ float2 scale(float2 v, float f) { return mul2(v, dup2(f)); }
 template <typename CT, typename R>
 __device__ __forceinline__ CT scale(CT v, R f)
 {
@@ -125,6 +170,8 @@ __device__ __forceinline__ CT scale(CT v, R f)
     }
 }
 // c + a L, a real
+__device__ __forceinline__ float2 axpy(const float2 &c, float a, const float2 &L) { return fma2(dup2(a), L, c); }
+__device__ __forceinline__ float axpy(float c, float a, float L) { return __fmaf_rn(a, L, c); }
 template <typename CT, typename R>
 __device__ __forceinline__ CT axpy(const CT &c, R a, const CT &L)
 {
@@ -154,6 +201,7 @@ __device__ __forceinline__ bool finite_v(const CT &v)
     else
         return isfinite(v);
 }
+__device__ __forceinline__ float2 vadd(const float2 &a, const float2 &b) { return add2(a, b); }
 template <typename CT>
 __device__ __forceinline__ CT vadd(const CT &a, const CT &b)
 {
@@ -168,6 +216,15 @@ __device__ __forceinline__ CT vadd(const CT &a, const CT &b)
 }
 // L + wxy exy + wxz exz + wyz eyz: the edge terms of App. B's 19-point
 // stencil added to its face-and-centre part
+__device__ __forceinline__ float2 edgev(const float2 &L, const float2 &exy, const float2 &exz, const float2 &eyz,
+                                        float wxy, float wxz, float wyz)
+{
+    return fma2(dup2(wyz), eyz, fma2(dup2(wxz), exz, fma2(dup2(wxy), exy, L)));
+}
+__device__ __forceinline__ float edgev(float L, float exy, float exz, float eyz, float wxy, float wxz, float wyz)
+{
+    return __fmaf_rn(wyz, eyz, __fmaf_rn(wxz, exz, __fmaf_rn(wxy, exy, L)));
+}
 template <typename CT, typename R>
 __device__ __forceinline__ CT edgev(const CT &L, const CT &exy, const CT &exz, const CT &eyz, R wxy, R wxz, R wyz)
 {
@@ -181,11 +238,32 @@ __device__ __forceinline__ CT edgev(const CT &L, const CT &exy, const CT &exz, c
     }
 }
 // one component of the 7-point Laplacian (Eq. (B1)) from opposite-neighbour
-// sums: (x- + x+)/hx^2 + (y- + y+)/hy^2 + (z- + z+)/hz^2 - c6 c
+// sums: (x- + x+)/hx^2 + (y- + y+)/hy^2 + (z- + z+)/hz^2 - c6 c.  In single
+// precision the order of the roundings is fixed explicitly, the same as the
+// packed complex64 form (lapv below), so that a real-valued float state and a
+// complex64 state with zero imaginary part compute bit-identical values.
+__device__ __forceinline__ float lap1(float xp, float xm, float yp, float ym, float zp, float zm, float c, float ihx2,
+                                      float ihy2, float ihz2, float c6)
+{
+    float t = __fmul_rn(__fadd_rn(xp, xm), ihx2);
+    t = __fmaf_rn(__fadd_rn(yp, ym), ihy2, t);
+    t = __fmaf_rn(__fadd_rn(zp, zm), ihz2, t);
+    return __fmaf_rn(-c6, c, t);
+}
 template <typename R>
 __device__ __forceinline__ R lap1(R xp, R xm, R yp, R ym, R zp, R zm, R c, R ihx2, R ihy2, R ihz2, R c6)
 {
     return (xp + xm) * ihx2 + (yp + ym) * ihy2 + (zp + zm) * ihz2 - c6 * c;
+}
+// complex64: the same operations as lap1 on both parts at once
+__device__ __forceinline__ float2 lapv(const float2 &xp, const float2 &xm, const float2 &yp, const float2 &ym,
+                                       const float2 &zp, const float2 &zm, const float2 &c, float ihx2, float ihy2,
+                                       float ihz2, float c6)
+{
+    float2 t = mul2(add2(xp, xm), dup2(ihx2));
+    t = fma2(add2(yp, ym), dup2(ihy2), t);
+    t = fma2(add2(zp, zm), dup2(ihz2), t);
+    return fma2(dup2(-c6), c, t);
 }
 template <typename CT, typename R>
 __device__ __forceinline__ CT lapv(const CT &xp, const CT &xm, const CT &yp, const CT &ym, const CT &zp, const CT &zm,
@@ -365,8 +443,23 @@ struct WarpSpace {
     __device__ __forceinline__ static int slot(int hx, int y, int z) { return hx + SX * ((y + 1) + TY * (z + 1)); }
     __device__ __forceinline__ static int h(int y, int z) { return NP == 19 ? (y + 1) + TY * (z + 1) : y + BY * z; }
     uint4 units[UPS][PSTR];
-    CT xlo[XH];  // x = -1
-    CT xhi[XH];  // x = BX
+    // x halos.  7-point: per row the 16-byte unit of the neighbour segment that
+    // holds the halo cell (cell 3 of the -x brick's last segment of the row,
+    // cell 0 of the +x brick's first), filled by cp.async like the tile; the
+    // 19-point stencil keeps single cells (also on its halo rows and planes).
+    static constexpr int XW = NP == 19 ? (int)sizeof(CT) : 16;
+    alignas(16) unsigned char xlo_[XH * XW];  // x = -1
+    alignas(16) unsigned char xhi_[XH * XW];  // x = BX
+    __device__ __forceinline__ CT xm_cell(int h) const  // the cell at x = -1 of row h
+    {
+        return reinterpret_cast<const CT *>(xlo_ + h * XW)[NP == 19 ? 0 : CPU_ - 1];
+    }
+    __device__ __forceinline__ CT xp_cell(int h) const  // the cell at x = BX of row h
+    {
+        return reinterpret_cast<const CT *>(xhi_ + h * XW)[0];
+    }
+    __device__ __forceinline__ CT *xm_slot(int h) { return reinterpret_cast<CT *>(xlo_ + h * XW) + (NP == 19 ? 0 : CPU_ - 1); }
+    __device__ __forceinline__ CT *xp_slot(int h) { return reinterpret_cast<CT *>(xhi_ + h * XW); }
     alignas(16) BrickRec rec[NR];
 #if GPE_REC_AHEAD
     BrickRec nrec[NR];  // records of the warp's next brick, fetched ahead
@@ -611,6 +704,19 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
                    W::slot(hx, (e & 1) ? BY : -1, (e & 2) ? BZ : -1), t % LPS);
         }
     }
+    // -x / +x faces, 7-point, identity transform: per row one 16-byte unit
+    // (the one holding cell 3 of the -x brick's segment, or cell 0 of the +x
+    // brick's) by cp.async; absent segments give a zero unit
+    if constexpr (NP != 19 && ASYNC) {
+        for (int u = lane; u < 2 * BY * BZ; u += 32) {
+            const int face = u / (BY * BZ), v_ = u % (BY * BZ);
+            const int y = v_ % BY, z = v_ / BY;
+            uint32_t j = 0;
+            const bool ok = seg_index(ws.rec[1 + face], (face == 0 ? S::SX - 1 : 0) + S::SX * y + S::PLANE * z, j);
+            const char *g = reinterpret_cast<const char *>(src + (ok ? j : 0u)) + (face == 0 ? 16 * (W::UPS - 1) : 0);
+            cp_async16((face == 0 ? ws.xlo_ : ws.xhi_) + 16 * W::h(y, z), g, ok);
+        }
+    } else
     // -x / +x faces: single cells (x = BX-1 of the -x brick, x = 0 of the +x
     // brick); for the 19-point stencil also on the halo rows and planes,
     // from the xy-edge (records 7..10) and xz-edge (11..14) neighbours
@@ -636,7 +742,7 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
                     v = xf(ld1<CG>(src + j), j);
                 }
             }
-            (face == 0 ? ws.xlo : ws.xhi)[W::h(y, z)] = v;
+            *(face == 0 ? ws.xm_slot(W::h(y, z)) : ws.xp_slot(W::h(y, z))) = v;
         }
     }
     cp_async_wait_all();
@@ -654,8 +760,8 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
         ws.get(sl + W::ROW, yp);
         ws.get(sl - W::PLANE, zm);
         ws.get(sl + W::PLANE, zp);
-        const CT xm = hx == 0 ? ws.xlo[hrow] : ws.last(sl - 1);
-        const CT xp = hx == S::SX - 1 ? ws.xhi[hrow] : ws.first(sl + 1);
+        const CT xm = hx == 0 ? ws.xm_cell(hrow) : ws.last(sl - 1);
+        const CT xp = hx == S::SX - 1 ? ws.xp_cell(hrow) : ws.first(sl + 1);
         if constexpr (NP != 19) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -675,9 +781,9 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
             const R ax = ihx2 - (R)2 * (wxy + wxz), ay = ihy2 - (R)2 * (wxy + wyz), az = ihz2 - (R)2 * (wxz + wyz);
             const R c19 = c6 - (R)4 * (wxy + wxz + wyz);
             const int row = sl / S::SX, y = row % W::TY - 1, z = row / W::TY - 1;
-            auto left = [&](int s2, int yy, int zz) { return hx == 0 ? ws.xlo[W::h(yy, zz)] : ws.last(s2 - 1); };
+            auto left = [&](int s2, int yy, int zz) { return hx == 0 ? ws.xm_cell(W::h(yy, zz)) : ws.last(s2 - 1); };
             auto right = [&](int s2, int yy, int zz) {
-                return hx == S::SX - 1 ? ws.xhi[W::h(yy, zz)] : ws.first(s2 + 1);
+                return hx == S::SX - 1 ? ws.xp_cell(W::h(yy, zz)) : ws.first(s2 + 1);
             };
             const CT yml = left(sl - W::ROW, y - 1, z), ymr = right(sl - W::ROW, y - 1, z);
             const CT ypl = left(sl + W::ROW, y + 1, z), ypr = right(sl + W::ROW, y + 1, z);
@@ -886,9 +992,41 @@ struct Rk4Body {
         if constexpr (st == 3) ld4<CG>(a.w + idx, p.y);
         return p;
     }
-    __device__ __forceinline__ void operator()(uint32_t idx, const P &p, const CT (&c)[4], const CT (&L)[4]) const
+    // the stage's new values o (and, stage 1, the partial sum wv) of the
+    // segment with values c, Laplacians L and operands p
+    __device__ __forceinline__ void compute(const P &p, const CT (&c)[4], const CT (&L)[4], CT (&o)[4],
+                                            CT (&wv)[4]) const
     {
-        CT o[4], wv[4];
+        if constexpr (std::is_same<R, float>::value) {
+            // complex64: both parts at once (f32x2), the same operations as the
+            // scalar form below
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!(p.V0[i] < (R)INFINITY)) {
+                    o[i] = czero<CT>();
+                    wv[i] = czero<CT>();
+                    continue;
+                }
+                R V = p.V0[i];
+                if constexpr (BLEND) V = ((R)1 - s) * p.V0[i] + s * p.V1[i];
+                const R w = V + a.g * (c[i].x * c[i].x + c[i].y * c[i].y);
+                const float2 h = fma2(dup2(w), c[i], mul2(dup2(-0.5f), L[i]));   // (hr, hi)
+                const float2 hs = make_float2(h.y, h.x);                           // (hi, hr)
+                const float2 kk = make_float2(k, -k);                              // f = (hi, -hr)
+                if constexpr (st == 0) {
+                    o[i] = fma2(kk, hs, c[i]);
+                } else if constexpr (st < 3) {
+                    o[i] = fma2(kk, hs, p.y[i]);
+                    if constexpr (st == 1) wv[i] = fma2(dup2(2.0f), o[i], sub2(c[i], p.y[i]));
+                } else {
+                    const float2 x = add2(p.y[i], c[i]);
+                    const float2 t3 = dup2(1.0f / 3.0f);
+                    const float2 q = mul2(x, t3);
+                    o[i] = fma2(kk, hs, fma2(fma2(dup2(-3.0f), q, x), t3, q));  // div3 of both parts
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (!(p.V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
@@ -917,6 +1055,11 @@ struct Rk4Body {
                 o[i].y = div3(p.y[i].y + c[i].y) - k * hr;
             }
         }
+    }
+    __device__ __forceinline__ void operator()(uint32_t idx, const P &p, const CT (&c)[4], const CT (&L)[4]) const
+    {
+        CT o[4], wv[4];
+        compute(p, c, L, o, wv);
         if constexpr (st == 1) st4(a.w + idx, wv);
         st4(yout + idx, o);
     }
@@ -933,9 +1076,23 @@ __device__ __forceinline__ void rk4_brick(const RkArgs<R> &a, const GridView &G,
                                 [&](uint32_t idx) { return body.load(idx); }, body);
 }
 
+// Programmatic dependent launch: a stage kernel launched with programmatic
+// stream serialisation may become resident while the previous stage's last
+// blocks still run.  It waits here until that grid has completed and its
+// writes are visible, then lets its own dependent launch in turn (once every
+// block of this grid has passed this point, so at most two grids share the
+// GPU and none waits for a block that cannot become resident).  Without a
+// programmatic dependency both instructions return at once.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename R, int BX, int BY, int BZ, bool BLEND, int ST, int NP = 7>
 __global__ void GPE_BOUNDS_NP(R) k_rk4_staged(const RkArgs<R> a, const GridView G)
 {
+    pdl_enter();
     constexpr int NW = KernelCfg<R>::NW;
     auto &ws = warp_space<R, BX, BY, BZ, typename Cx<R>::T, NP>();
     const int warp = threadIdx.x >> 5;

@@ -28,9 +28,9 @@
 #include <unordered_map>
 #include <vector>
 
-#include "flat.cuh"
 #include "gpe_internal.cuh"
 #include "kernels.cuh"
+#include "pair.cuh"
 
 namespace gpe {
 
@@ -85,6 +85,26 @@ template <typename R, typename K>
 static int blocks_for(K kernel, const gpe_grid *g, size_t smem)
 {
     return blocks_for_nw(kernel, g, smem, KernelCfg<R>::NW);
+}
+
+// Launch a stage kernel; with pdl, with programmatic stream serialisation so
+// that it can become resident during the previous kernel's tail (the kernel
+// itself waits for that grid before reading its output: pdl_enter).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_stage(void (*k)(KArgs...), unsigned grid, unsigned threads, size_t smem, cudaStream_t s,
+                                bool pdl, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 // ------------------------------------------------------------ wavefront sync
@@ -693,36 +713,45 @@ static int replay_graph(gpe_state *st, int which, uint64_t key, int nodes, int64
 
 __global__ void k_add_scalar(double *p, double v) { *p += v; }
 
-// ------------------------------------------------------------ segment table (FLAT schedule)
-// segtab[k] = brick << 7 | q for the k-th stored segment of the packed run
-// (brick b's stored segments start at rec[b].off / 4, in increasing q)
-__global__ void k_segtab(const BrickRec *rec, int64_t nb, int nseg_brick, uint32_t *segtab)
+// ------------------------------------------------------------ neighbour ids (PAIR schedule)
+// nbr18[18 b + k]: the face neighbours (-x +x -y +y -z +z) and the 12 edge
+// neighbours (xy (-1,-1,0) (+1,-1,0) (-1,+1,0) (+1,+1,0); xz (-1,0,-1)
+// (+1,0,-1) (-1,0,+1) (+1,0,+1); yz (0,-1,-1) (0,+1,-1) (0,-1,+1) (0,+1,+1))
+// of brick b, -1 if absent
+__global__ void k_nbr18(int64_t nb, const int32_t *org, int bx, int by, int bz, int64_t nbx, int64_t nby, int64_t nbz,
+                        const int32_t *bvol, const int32_t *nbr6, int32_t *out)
 {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const BrickRec r = rec[b];
-    uint32_t k = r.off / 4u;
-    for (int q = 0; q < nseg_brick; ++q)
-        if ((r.m[q >> 5] >> (q & 31)) & 1u) segtab[k++] = ((uint32_t)b << 7) | (uint32_t)q;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nb) return;
+    const int8_t d[12][3] = {{-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}, {-1, 0, -1}, {1, 0, -1},
+                             {-1, 0, 1},  {1, 0, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+    for (int k = 0; k < 6; ++k) out[18 * id + k] = nbr6[6 * id + k];
+    const int64_t cx = org[3 * id] / bx, cy = org[3 * id + 1] / by, cz = org[3 * id + 2] / bz;
+    for (int e = 0; e < 12; ++e) {
+        const int64_t x = cx + d[e][0], y = cy + d[e][1], z = cz + d[e][2];
+        int32_t r = -1;
+        if (x >= 0 && x < nbx && y >= 0 && y < nby && z >= 0 && z < nbz) r = bvol[x + nbx * (y + nby * z)];
+        out[18 * id + 6 + e] = r;
+    }
 }
 
-static int ensure_segtab(gpe_grid *g)
+static int ensure_nbr18(gpe_grid *g)
 {
-    if (g->d_segtab) return GPE_OK;
-    if (g->nb >= (1LL << 25)) return fail(GPE_ERR_ARG, "too many bricks (%lld) for the FLAT schedule", (long long)g->nb);
-    uint32_t *t = nullptr;
-    GPE_TRY(dev_alloc_t(&t, (size_t)std::max<int64_t>(1, g->n_packed / 4)));
+    if (g->d_nbr18) return GPE_OK;
+    int32_t *t = nullptr;
+    GPE_TRY(dev_alloc_t(&t, (size_t)std::max<int64_t>(1, 18 * g->nb)));
     if (g->nb > 0) {
-        k_segtab<<<(unsigned)((g->nb + 255) / 256), 256, 0, cudaStreamLegacy>>>(g->d_rec, g->nb, g->bc / 4, t);
+        k_nbr18<<<(unsigned)((g->nb + 255) / 256), 256, 0, cudaStreamLegacy>>>(
+            g->nb, g->d_org, g->bx, g->by, g->bz, g->nbx, g->nby, g->nbz, g->d_bvol, g->d_nbr, t);
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
-        count_launch();
         if (e != cudaSuccess) {
             dev_free(t);
-            return cuda_fail(e, "k_segtab", __FILE__, __LINE__);
+            return cuda_fail(e, "k_nbr18", __FILE__, __LINE__);
         }
     }
-    g->d_segtab = t;
+    g->d_nbr18 = t;
     return GPE_OK;
 }
 
@@ -789,21 +818,33 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
         }
         return GPE_OK;
     }
-    if (g->sched == GPE_SCHED_FLAT) {
-        GPE_TRY(ensure_segtab(const_cast<gpe_grid *>(g)));
-        const FlatView F{g->d_segtab, g->d_rec7, g->n_packed / 4};
-        using RF = Rk4Flat<R, BX, BY, BZ>;
-        typename RF::K kf[4];
-        for (int stg = 0; stg < 4; ++stg) kf[stg] = RF::get(blend, stg);
-        const unsigned nbf = (unsigned)std::max<int64_t>(1, (F.nseg + RF::THREADS - 1) / RF::THREADS);
+    if (g->sched == GPE_SCHED_PAIR) {
+        // two launches per step (stages 0+1, 2+3); the state alternates between
+        // the psi buffer and work buffer 0 (unused by this schedule otherwise)
+        GPE_TRY(ensure_nbr18(const_cast<gpe_grid *>(g)));
+        const PairView P{g->d_rec, g->d_nbr18, g->nb};
+        using RP = Rk4Pairs<R, BX, BY, BZ>;
+        typename RP::K kp[2] = {RP::get(blend, 0), RP::get(blend, 1)};
+        const size_t psm = pair_smem<R, BX, BY, BZ>();
+        int nbp[2];
+        for (int i = 0; i < 2; ++i)
+            nbp[i] = (int)std::max<int64_t>(
+                1, std::min<int64_t>(g->nb, (int64_t)g->nsm * per_sm_for(kp[i], PAIR_THREADS, psm)));
+        CT *bufA = (CT *)st->d_psi, *bufB = (CT *)st->d_work[0];
+        // cnt steps from bufA; after an odd count psi is copied back to bufA
         auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
             for (int64_t n = 0; n < cnt; ++n) {
-                a.t_off = (double)n * p->dt;
-                for (int stg = 0; stg < 4; ++stg) {
-                    kf[stg]<<<nbf, RF::THREADS, 0, cs>>>(a, F);
+                RkArgs<R> an = a;
+                an.t_off = (double)n * p->dt;
+                an.y0 = (n % 2 == 0) ? bufA : bufB;
+                CT *out = (n % 2 == 0) ? bufB : bufA;
+                for (int pass = 0; pass < 2; ++pass) {
+                    kp[pass]<<<nbp[pass], PAIR_THREADS, psm, cs>>>(an, P, out);
                     GPE_LAUNCH_CHECK();
                 }
             }
+            if (cnt % 2)
+                GPE_TRY_CUDA(cudaMemcpyAsync(bufA, bufB, (size_t)g->n_packed * sizeof(CT), cudaMemcpyDeviceToDevice, cs));
             return GPE_OK;
         };
         int64_t left = nsteps;
@@ -821,7 +862,7 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
                 }
                 return GPE_OK;
             };
-            GPE_TRY(replay_graph(st, 0, key, 4 * G_ + (blend ? 1 : 0), nsteps / G_, s, rec_block));
+            GPE_TRY(replay_graph(st, 0, key, 2 * G_ + (blend ? 1 : 0), nsteps / G_, s, rec_block));
             left = nsteps % G_;
         }
         return record(s, left);
@@ -838,7 +879,9 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
         for (int64_t n = 0; n < cnt; ++n) {
             a.t_off = (double)n * p->dt;
             for (int stg = 0; stg < 4; ++stg) {
-                k[stg]<<<nblk[stg], RS::THREADS, RS::smem(), cs>>>(a, G);
+                // stage 0 follows the scalar kernels of a ramp (no programmatic edge)
+                const bool pdl = st->pdl && !(blend && n == 0 && stg == 0);
+                GPE_TRY_CUDA(launch_stage(k[stg], (unsigned)nblk[stg], RS::THREADS, RS::smem(), cs, pdl, a, G));
                 GPE_LAUNCH_CHECK();
             }
         }
@@ -1082,9 +1125,10 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
         const int nba = blocks_for<R>(ka, g, smem), nbb = blocks_for<R>(kb, g, smem);
         auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
             for (int64_t n = 0; n < cnt; ++n) {
-                ka<<<nba, th, smem, cs>>>(a, G);
+                GPE_TRY_CUDA(launch_stage(ka, (unsigned)nba, th, smem, cs, st->pdl && n > 0, a, G));
                 GPE_LAUNCH_CHECK();
-                kb<<<nbb, th, smem, cs>>>(a, G, st->red.partials, st->red.counter);
+                GPE_TRY_CUDA(launch_stage(kb, (unsigned)nbb, th, smem, cs, st->pdl, a, G, st->red.partials,
+                                          st->red.counter));
                 GPE_LAUNCH_CHECK();
             }
             return GPE_OK;

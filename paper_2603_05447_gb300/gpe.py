@@ -35,7 +35,7 @@ ERROR_NAMES = {v: k for k, v in dict(
 
 GPE_MASK_CELL, GPE_MASK_BRICK = 0, 1
 GPE_ORDER_ZMAJOR, GPE_ORDER_MORTON = 0, 1
-GPE_SCHED_STAGED, GPE_SCHED_WAVE, GPE_SCHED_WAVE2 = 0, 1, 2
+GPE_SCHED_STAGED, GPE_SCHED_WAVE, GPE_SCHED_WAVE2, GPE_SCHED_PAIR = 0, 1, 2, 3
 GPE_F64, GPE_F32 = 1, 2
 GPE_POT_HARMONIC, GPE_POT_ELLIPSOID_SHELL = 1, 2
 GPE_C128, GPE_C64, GPE_R64, GPE_R32 = 1, 2, 3, 4

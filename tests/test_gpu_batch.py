@@ -182,3 +182,66 @@ def test_autotune_returns_a_timed_valid_layout():
     gpe.gpe_step_real(st, gpe.real_params(wl.g, wl.stable_dt()), 2)
     gpe.gpe_state_destroy(st)
     gpe.gpe_grid_destroy(grid)
+
+
+def _c4_small_states(dtype):
+    """Four seeded shells of the batch family (radius scale 40 cells instead
+    of 360: boxes of 76-104 cells, 1e5-2.5e5 active), parabolic initial
+    profiles, 8^3 bricks, as the batch benchmark builds them."""
+    shells = inputs.batch_shells(4, seed=4, scale_cells=40.0)
+    made, params = [], []
+    for wl in shells:
+        b = wl.box
+        g = gpe.gpe_grid_create_analytic(gpe.make_box(b.nx, b.ny, b.nz, b.hx),
+                                         gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes),
+                                         wl.V_cut, gpe.make_opts((8, 8, 8)))
+        idx, ii, jj, kk = gpe.packed_coords(g)
+        psi = np.zeros(gpe.gpe_grid_get_info(g).n_packed, np.complex128)
+        psi[idx] = np.sqrt(np.maximum(wl.mu0 - wl.potential(b.x0 + ii * b.hx, b.y0 + jj * b.hy, b.z0 + kk * b.hz),
+                                      0.0) / wl.g)
+        st = gpe.gpe_state_create(g, dtype)
+        gpe.gpe_state_load(st, np.ascontiguousarray(psi.astype(np.complex64 if dtype == gpe.GPE_C64 else
+                                                                np.complex128)), gpe.GPE_LAYOUT_COMPACT)
+        made.append((g, st))
+        params.append(gpe.gpe_imag_params(wl.g, wl.stable_dt() * 20, 1.0))
+    return shells, made, params
+
+
+def test_batch_ground_states_at_dmu_1e8_and_the_complex64_floor():
+    """The batch configuration's tolerance, |mu_n - mu_(n-1)| < 1e-8 between
+    checks (absolute, mu in FP64), on four small shells of that family.  The
+    complex128 solves converge.  The complex64 solves either converge (the
+    single-precision iteration can land on an exact fixed point, |dmu| = 0)
+    or stop at max_steps on their rounding floor: |dmu| between further
+    checks is then at most a few FP32 units of mu (2e-7 relative).  Either
+    way their mu equals the complex128 value to 1e-6 relative.  bench.py
+    --workload batch measures the same floor on the large shells."""
+    res = {}
+    for dtype in (gpe.GPE_C128, gpe.GPE_C64):
+        shells, made, params = _c4_small_states(dtype)
+        batch = gpe.gpe_batch_create([st for _, st in made])
+        try:
+            rc, conv, steps, obs = gpe.gpe_batch_ground_state(batch, params, 1e-8, 50, 5000, check=False)
+            mus = [o["mu"] for o in obs]
+            if dtype == gpe.GPE_C128:
+                assert rc == gpe.GPE_OK and all(conv), (conv, steps)
+                assert all(n < 5000 for n in steps)
+            else:
+                assert rc in (gpe.GPE_OK, gpe.GPE_ERR_NOT_CONVERGED)
+                for (g, st), p, wl, c, mu in zip(made, params, shells, conv, mus):
+                    if c:
+                        continue
+                    m = []
+                    for _ in range(7):
+                        gpe.gpe_step_imag(st, p, 50)
+                        m.append(gpe.gpe_observables(st, wl.g)["mu"])
+                    floor = float(np.median(np.abs(np.diff(m))))
+                    assert floor <= 2e-7 * abs(mu), (floor, mu)
+            res[dtype] = mus
+        finally:
+            gpe.gpe_batch_destroy(batch)
+            for g, st in made:
+                gpe.gpe_state_destroy(st)
+                gpe.gpe_grid_destroy(g)
+    for m64, m128 in zip(res[gpe.GPE_C64], res[gpe.GPE_C128]):
+        assert abs(m64 - m128) <= 1e-6 * abs(m128)

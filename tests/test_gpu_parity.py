@@ -325,6 +325,36 @@ def test_rk4_c64_matches_oracle(name):
         assert rel_l2(G.dense(), oracle_rk4(case, og, psi32, 10)) <= C64_TOL_10
 
 
+@pytest.mark.parametrize("name", ["harmonic64", "ragged", "shell64", "single"])
+def test_rk4_c64_8x8x4_matches_oracle_and_the_8x8x8_tile_kernels(name):
+    """complex64 on 8x8x4 bricks runs the register-tile stage kernels (the
+    brick in the warp's registers, neighbours by shuffles); 8x8x8 bricks run
+    the shared-memory tile kernels.  Same arithmetic per cell: identical
+    bits, and both within the complex64 tolerance of the oracle."""
+    case = CASES[name]()
+    og = oracle_grid(case)
+    outs = []
+    for brick in ((8, 8, 4), (8, 8, 8)):
+        with Gpu(case, dtype=gpe.GPE_C64, brick=brick) as G:
+            psi32 = G.dense()
+            gpe.gpe_step_real(G.state, gpe.real_params(case.g, case.dt), 10)
+            outs.append(G.dense())
+    assert rel_l2(outs[0], oracle_rk4(case, og, psi32, 10)) <= C64_TOL_10
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_rk4_c64_8x8x4_ramp_blend_matches_the_tile_kernels():
+    case = ramp_case()
+    t0 = 7 * case.dt
+    outs = []
+    for brick in ((8, 8, 4), (8, 8, 8)):
+        with Gpu(case, dtype=gpe.GPE_C64, brick=brick) as G:
+            p = gpe.real_params(case.g, case.dt, gpe.GPE_V_BLEND, case.knots, case.T)
+            gpe.gpe_step_real(G.state, p, 12, t0)
+            outs.append(G.dense())
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_rk4_ramp_blend_matches_oracle():
     case = ramp_case()
     og = oracle_grid(case)
