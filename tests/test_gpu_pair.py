@@ -120,3 +120,47 @@ def test_pair_grid_runs_the_other_calls_staged():
             obs.append(gpe.gpe_observables(G.state, case.g))
     assert np.array_equal(outs[0], outs[1])
     assert obs[0] == obs[1]
+
+
+def test_pair_grid_serves_traces_and_the_ramp_gradient_as_staged():
+    """Calls built on gpe_step_real (the observables trace, the adjoint's
+    checkpointed forward run) give the same results on a PAIR grid; the
+    adjoint's backward recomputation runs the staged kernels, whose bits the
+    PAIR forward run reproduces."""
+    case = ramp_case()
+    p = gpe.real_params(case.g, case.dt, gpe.GPE_V_BLEND, case.knots, case.T)
+    res = []
+    for sched in (gpe.GPE_SCHED_STAGED, PAIR):
+        with Gpu(case, sched=sched, brick=(8, 8, 4)) as G:
+            tg = gpe.gpe_state_create(G.grid, gpe.GPE_C128)
+            try:
+                gpe.gpe_state_copy(tg, G.state)
+                trace = gpe.gpe_step_real_traced(G.state, p, 9, 4)
+                G.load(case.psi)
+                tape = gpe.gpe_ramp_forward(G.state, p, 21, 0.0, 8)
+                loss, grad = gpe.gpe_ramp_backward(tape, tg, 16)
+                gpe.gpe_tape_destroy(tape)
+            finally:
+                gpe.gpe_state_destroy(tg)
+            res.append((trace, loss, grad))
+    assert res[0][0] == res[1][0]
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
+
+
+def test_pair_schedule_on_a_19_point_grid_runs_the_staged_19_point_step():
+    case = ragged_shell()
+    outs = []
+    for sched in (gpe.GPE_SCHED_STAGED, PAIR):
+        opts = gpe.make_opts((8, 8, 4), sched=sched, stencil=19)
+        grid = gpe.gpe_grid_create_dense(case.gbox, case.V, case.V_cut, opts)
+        st = gpe.gpe_state_create(grid, gpe.GPE_C128)
+        try:
+            gpe.gpe_state_load(st, np.ascontiguousarray(case.psi), gpe.GPE_LAYOUT_DENSE)
+            gpe.gpe_step_real(st, gpe.real_params(case.g, case.dt), 3)
+            out = np.zeros(case.box.shape, np.complex128)
+            gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_DENSE)
+            outs.append(out)
+        finally:
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(grid)
+    assert np.array_equal(outs[0], outs[1])
