@@ -531,7 +531,8 @@ typedef struct gpe_tune_result {
 } gpe_tune_result;
 
 /* Time every candidate layout (brick 8x8x8, 8x8x4, 8x4x4) and schedule
- * (staged; wavefront with 2-8 bricks per task) on the grid that
+ * (staged; wavefront with 2-8 bricks per task; for GPE_TUNE_REAL also the RK4
+ * stages fused in pairs, GPE_SCHED_PAIR, on 8x8x4 bricks) on the grid that
  * gpe_grid_create_analytic(box, pot, V_cut) builds, for `nsteps` real-time
  * (RK4) or imaginary-time steps of a state of type dtype, and return the
  * fastest in *best (use its fields in gpe_grid_opts).  all (room for 8

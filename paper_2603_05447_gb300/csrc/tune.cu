@@ -2,7 +2,8 @@
 //
 // For an analytic potential, cutoff, state type and step kind, builds the grid
 // with each candidate brick shape (8x8x8, 8x8x4, 8x4x4) and schedule (staged;
-// wavefront with 2 or 8 bricks per task), times `nsteps` steps with CUDA
+// wavefront with 2 or 8 bricks per task; for real time also the RK4 stages
+// fused in pairs), times `nsteps` steps with CUDA
 // events after one warm-up step, and returns the fastest in active-cell-steps
 // per second.  Results are cached per (state type, step kind, size class =
 // round(2 log2 n_active)) for the life of the process.
@@ -49,10 +50,12 @@ extern "C" int gpe_autotune(const gpe_box *box, const gpe_potential *pot, double
     struct Cand {
         int bx, by, bz, sched, chunk;
     };
+    // the last candidate, RK4 stages fused in pairs (fusion depth 2), applies
+    // to real-time steps only
     const Cand cands[] = {{8, 8, 8, GPE_SCHED_STAGED, 0}, {8, 8, 4, GPE_SCHED_STAGED, 0}, {8, 4, 4, GPE_SCHED_STAGED, 0},
                           {8, 8, 8, GPE_SCHED_WAVE, 2},   {8, 8, 8, GPE_SCHED_WAVE, 8},   {8, 8, 4, GPE_SCHED_WAVE, 4},
-                          {8, 4, 4, GPE_SCHED_WAVE, 8}};
-    const int nc = (int)(sizeof cands / sizeof cands[0]);
+                          {8, 4, 4, GPE_SCHED_WAVE, 8},   {8, 8, 4, GPE_SCHED_PAIR, 0}};
+    const int nc = (int)(sizeof cands / sizeof cands[0]) - (mode == GPE_TUNE_REAL ? 0 : 1);
     std::vector<gpe_tune_result> res;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GPE_TRY_CUDA(cudaEventCreate(&e0));

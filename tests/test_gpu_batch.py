@@ -171,7 +171,8 @@ def test_autotune_returns_a_timed_valid_layout():
     box = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
     pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
     best, allr = gpe.gpe_autotune(box, pot, wl.V_cut, gpe.GPE_C64, gpe.GPE_TUNE_REAL, 5)
-    assert len(allr) == 7 and best["cell_steps_per_s"] == max(r["cell_steps_per_s"] for r in allr)
+    assert len(allr) == 8 and best["cell_steps_per_s"] == max(r["cell_steps_per_s"] for r in allr)
+    assert any(r["sched"] == gpe.GPE_SCHED_PAIR for r in allr)
     assert (best["bx"], best["by"], best["bz"]) in {(8, 8, 8), (8, 8, 4), (8, 4, 4)}
     cached, none = gpe.gpe_autotune(box, pot, wl.V_cut, gpe.GPE_C64, gpe.GPE_TUNE_REAL, 5, timings=False)
     assert none == [] and cached == best
