@@ -491,7 +491,7 @@ def _run_ours(args, torch, world, rank, local):
                      "kernel": {0: "RK4 step (k_rk4_staged, four launches per step)",
                                 1: "RK4 step (k_rk4_wave, one launch per step)",
                                 2: "RK4 step (k_rk4_wave, two launches of two stages per step)",
-                                3: "RK4 step (k_rk4_pair2, two launches of two fused stages per step)"}[args.sched],
+                                3: "RK4 step (k_rk4_fused, two launches of two fused stages per step)"}[args.sched],
                      "peak_kind": peak_kind,
                      "alg_bytes_per_cell_step": B_ALG["c64"], "ms_per_rk4_step": rk_ms,
                      "traffic_gbs": traffic / (rk_ms / 1e3) / 1e9 if traffic else None,

@@ -398,7 +398,7 @@ __device__ __forceinline__ void pair_brick(PairSpace<typename Cx<R>::T, BX, BY, 
 }
 
 template <typename R, int BX, int BY, int BZ, bool BLEND, int PASS>
-__global__ void __launch_bounds__(PAIR_THREADS) k_rk4_pair2(const RkArgs<R> a, const PairView P,
+__global__ void __launch_bounds__(PAIR_THREADS) k_rk4_fused(const RkArgs<R> a, const PairView P,
                                                             typename Cx<R>::T *y1out)
 {
     using CT = typename Cx<R>::T;
@@ -410,12 +410,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_rk4_pair2(const RkArgs<R> a, c
 }
 
 template <typename R, int BX, int BY, int BZ>
-struct Rk4Pairs {
+struct Rk4Fused {
     using K = void (*)(RkArgs<R>, PairView, typename Cx<R>::T *);
     static K get(bool blend, int pass)
     {
-        static const K t[2][2] = {{k_rk4_pair2<R, BX, BY, BZ, false, 0>, k_rk4_pair2<R, BX, BY, BZ, false, 1>},
-                                  {k_rk4_pair2<R, BX, BY, BZ, true, 0>, k_rk4_pair2<R, BX, BY, BZ, true, 1>}};
+        static const K t[2][2] = {{k_rk4_fused<R, BX, BY, BZ, false, 0>, k_rk4_fused<R, BX, BY, BZ, false, 1>},
+                                  {k_rk4_fused<R, BX, BY, BZ, true, 0>, k_rk4_fused<R, BX, BY, BZ, true, 1>}};
         return t[blend ? 1 : 0][pass];
     }
 };

@@ -823,7 +823,7 @@ static int rk4_run(gpe_state *st, const gpe_real_params *p, int64_t nsteps, doub
         // the psi buffer and work buffer 0 (unused by this schedule otherwise)
         GPE_TRY(ensure_nbr18(const_cast<gpe_grid *>(g)));
         const PairView P{g->d_rec, g->d_nbr18, g->nb};
-        using RP = Rk4Pairs<R, BX, BY, BZ>;
+        using RP = Rk4Fused<R, BX, BY, BZ>;
         typename RP::K kp[2] = {RP::get(blend, 0), RP::get(blend, 1)};
         const size_t psm = pair_smem<R, BX, BY, BZ>();
         int nbp[2];
