@@ -450,14 +450,16 @@ def _run_ours(args, torch, world, rank, local):
     pinned_in = torch.empty(n_stored, dtype=torch.complex64, pin_memory=True)
     pinned_out = torch.empty(n_stored, dtype=torch.complex64, pin_memory=True)
     pinned_in.numpy()[:] = psi64
-    gpe.gpe_state_load(st64, pinned_in.numpy(), gpe.GPE_LAYOUT_COMPACT)
+    gpe.gpe_state_load(st64, pinned_in, gpe.GPE_LAYOUT_COMPACT)
     e2e_steps = max(2, min(args.steps, 3))
     barrier(world)
+    # the page-locked host tensors are passed as they are (a numpy view made
+    # inside the loop would add milliseconds of host time per call)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        gpe.gpe_state_load(st64, pinned_in.numpy(), gpe.GPE_LAYOUT_COMPACT)
+        gpe.gpe_state_load(st64, pinned_in, gpe.GPE_LAYOUT_COMPACT)
         gpe.gpe_step_real(st64, params, STEPS_PER_BENCH)
-        gpe.gpe_state_store(st64, pinned_out.numpy(), gpe.GPE_LAYOUT_COMPACT)
+        gpe.gpe_state_store(st64, pinned_out, gpe.GPE_LAYOUT_COMPACT)
         gpe.gpe_observables(st64, wl.g)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)

@@ -438,6 +438,42 @@ __global__ void k_zero_inactive(CT *psi, const double *V0, int64_t n)
         if (!(V0[s] < INFINITY)) psi[s] = czero<CT>();
 }
 
+// psi = src, zero on the inactive cells of stored segments, in one pass; src
+// may be page-locked host memory read in place by the GPU (its device view)
+template <typename CT>
+__global__ void k_load_zero(CT *psi, const CT *src, const double *V0, int64_t n)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        psi[s] = V0[s] < INFINITY ? src[s] : czero<CT>();
+}
+
+// The device view of page-locked host memory (NULL for pageable memory).
+// The driver is asked (cuPointerGetAttribute through its entry point): memory
+// page-locked by another CUDA runtime in the process (a framework's pinned
+// allocator) is known to the driver but not to this library's runtime.
+typedef int (*ptr_attr_fn)(void *data, int attribute, unsigned long long ptr);
+static const void *pinned_view(const void *p)
+{
+    static ptr_attr_fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<ptr_attr_fn>(f);
+        cudaGetLastError();
+        looked = true;
+    }
+    if (!fn) return nullptr;
+    const unsigned long long a = (unsigned long long)(uintptr_t)p;
+    unsigned int type = 0;
+    unsigned long long dptr = 0;
+    // attributes 2 (memory type; 1 = host) and 3 (device pointer)
+    if (fn(&type, 2, a) != 0 || type != 1u || fn(&dptr, 3, a) != 0 || dptr == 0) return nullptr;
+    return reinterpret_cast<const void *>((uintptr_t)dptr);
+}
+
 // ------------------------------------------------------------ state helpers
 int ensure_work(gpe_state *st, int n)
 {
@@ -1318,6 +1354,21 @@ extern "C" int gpe_state_load(gpe_state *st, const void *psi, int layout, int on
     cudaStream_t s = S(stream);
     const GridView G = view(g);
     if (layout == GPE_LAYOUT_COMPACT) {
+        // page-locked host input: read in place over the host link by one
+        // copy-and-zero kernel, which is faster than a staged memcpy there
+        const void *hv = on_device ? nullptr : pinned_view(psi);
+        if (hv) {
+            const unsigned nbk = (unsigned)g->nsm * 8;
+            switch (st->dtype) {
+            case GPE_C128: k_load_zero<double2><<<nbk, 256, 0, s>>>((double2 *)st->d_psi, (const double2 *)hv, g->d_V[0], g->n_packed); break;
+            case GPE_C64: k_load_zero<float2><<<nbk, 256, 0, s>>>((float2 *)st->d_psi, (const float2 *)hv, g->d_V[0], g->n_packed); break;
+            case GPE_R64: k_load_zero<double><<<nbk, 256, 0, s>>>((double *)st->d_psi, (const double *)hv, g->d_V[0], g->n_packed); break;
+            default: k_load_zero<float><<<nbk, 256, 0, s>>>((float *)st->d_psi, (const float *)hv, g->d_V[0], g->n_packed); break;
+            }
+            GPE_LAUNCH_CHECK();
+            GPE_TRY_CUDA(cudaStreamSynchronize(s));
+            return GPE_OK;
+        }
         GPE_TRY_CUDA(cudaMemcpyAsync(st->d_psi, psi, g->n_packed * st->elem,
                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         switch (st->dtype) {

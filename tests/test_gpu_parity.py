@@ -247,6 +247,35 @@ def test_load_store_roundtrip_is_exact(dtype):
         assert np.array_equal(np.where(case.mask, back, 0), back)
 
 
+@pytest.mark.parametrize("dtype", [gpe.GPE_C128, gpe.GPE_C64, gpe.GPE_R32])
+def test_compact_load_from_page_locked_host_memory_equals_pageable(dtype):
+    """Page-locked host input takes the direct copy-and-zero kernel; pageable
+    input the staged copy.  Same state either way, inactive entries zero."""
+    case = ragged_shell()
+    grid = gpe.gpe_grid_create_dense(case.gbox, case.V, case.V_cut)
+    st = gpe.gpe_state_create(grid, dtype)
+    try:
+        n = gpe.gpe_grid_get_info(grid).n_packed
+        rng = np.random.default_rng(3)
+        if dtype == gpe.GPE_R32:
+            host = rng.standard_normal(n).astype(np.float32) + 1.0
+        else:
+            cdt = np.complex128 if dtype == gpe.GPE_C128 else np.complex64
+            host = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(cdt) + 1.0
+        outs = []
+        for src in (np.ascontiguousarray(host), torch.from_numpy(host).pin_memory()):
+            gpe.gpe_state_load(st, src, gpe.GPE_LAYOUT_COMPACT)
+            out = np.zeros_like(host)
+            gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_COMPACT)
+            outs.append(out)
+        assert np.array_equal(outs[0], outs[1])
+        V = gpe.gpe_grid_potential(grid, 0)
+        assert np.all(outs[1][~np.isfinite(V)] == 0) and np.array_equal(outs[1][np.isfinite(V)], host[np.isfinite(V)])
+    finally:
+        gpe.gpe_state_destroy(st)
+        gpe.gpe_grid_destroy(grid)
+
+
 # ----------------------------------------------------------------- real time
 CASES = {"harmonic64": harmonic64, "shell64": shell, "ragged": ragged_shell, "single": single_cell}
 
