@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 STEPS_PER_BENCH = 100
+BATCH_STATES = {"c64": (2, np.complex64, "complex64"), "r32": (4, np.float32, "real float")}  # gpe state type ids
 FLOOR_CHECKS = 10                 # batch workload: checks that measure the complex64 |dmu| floor
 B_ALG = {"c64": 20.0, "c128": 40.0}   # algorithmic bytes per active cell-step (read psi, V; write psi)
 METRIC = "shell-grid GPE cell-steps/s: FP32 vs FP64 at stated error; % of HBM roofline"
@@ -424,7 +425,7 @@ def _run_ours(args, torch, world, rank, local):
     itp_ms = time_itp(gpe, torch, st64, ip, args.steps, args.warmup)
     itp = {"value": n_active / (itp_ms / 1e3), "unit": "cell-steps/s", "ms_per_itp_step": itp_ms,
            "achieved_gbs": B_ALG["c64"] * n_active / (itp_ms / 1e3) / 1e9,
-           "alg_bytes_per_cell_step": B_ALG["c64"], "launches_per_step": 2}
+           "alg_bytes_per_cell_step": B_ALG["c64"], "launches_per_step": 1 if args.sched == 3 else 2}
     gpe.gpe_state_load(st64, psi64, gpe.GPE_LAYOUT_COMPACT)
     # the same imaginary-time steps on a real-valued float state (|psi|)
     str_ = gpe.gpe_state_create(grid, gpe.GPE_R32)
@@ -433,6 +434,23 @@ def _run_ours(args, torch, world, rank, local):
     gpe.gpe_state_destroy(str_)
     itp["real_f32"] = {"value": n_active / (itpr_ms / 1e3), "unit": "cell-steps/s", "ms_per_itp_step": itpr_ms,
                        "achieved_gbs": 12.0 * n_active / (itpr_ms / 1e3) / 1e9, "alg_bytes_per_cell_step": 12.0}
+
+    # ---- the fused-pair schedule on the same shell (its own grid): RK4 in
+    # two launches per step, imaginary time in one
+    pair = None
+    if not args.quick and args.sched == 0:
+        gp = build_grid(gpe, wl, tuple(args.brick), 3, 0)
+        sp = gpe.gpe_state_create(gp, gpe.GPE_C64)
+        gpe.gpe_state_load(sp, psi64, gpe.GPE_LAYOUT_COMPACT)
+        _, rkp_ms = time_rk4(gpe, torch, sp, params, 2, 1, n_active, wl.g)
+        gpe.gpe_state_load(sp, psi64, gpe.GPE_LAYOUT_COMPACT)
+        itpp_ms = time_itp(gpe, torch, sp, ip, 2, 1)
+        pair = {"ms_per_rk4_step": rkp_ms, "rk4_launches_per_step": 2,
+                "rk4_achieved_gbs": B_ALG["c64"] * n_active / (rkp_ms / 1e3) / 1e9,
+                "ms_per_itp_step": itpp_ms, "itp_launches_per_step": 1,
+                "itp_achieved_gbs": B_ALG["c64"] * n_active / (itpp_ms / 1e3) / 1e9}
+        gpe.gpe_state_destroy(sp)
+        gpe.gpe_grid_destroy(gp)
 
     if args.quick:
         gpe.gpe_state_destroy(st64)
@@ -508,6 +526,7 @@ def _run_ours(args, torch, world, rank, local):
         "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": n_stored * 8,
                 "d2h_bytes_per_step": n_stored * 8 + 7 * 8},
         "itp": itp,
+        "pair_schedule": pair,
         "integrators": integ,
         "stencil19": st19,
         "gpu_launches": gpu_launches,
@@ -890,9 +909,9 @@ def run_extra(args):
                 idx, ii, jj, kk = gpe.packed_coords(g)
                 b = wl.box
                 x, y, z = b.x0 + ii * b.hx, b.y0 + jj * b.hy, b.z0 + kk * b.hz
-                psi = np.zeros(gpe.gpe_grid_get_info(g).n_packed, np.complex64)
+                psi = np.zeros(gpe.gpe_grid_get_info(g).n_packed, BATCH_STATES[args.batch_state][1])
                 psi[idx] = np.sqrt(np.maximum(wl.mu0 - wl.potential(x, y, z), 0.0) / wl.g)
-                st = gpe.gpe_state_create(g, gpe.GPE_C64)
+                st = gpe.gpe_state_create(g, BATCH_STATES[args.batch_state][0])
                 gpe.gpe_state_load(st, psi, gpe.GPE_LAYOUT_COMPACT)
                 states.append(st)
             batch = gpe.gpe_batch_create(states)
@@ -903,7 +922,7 @@ def run_extra(args):
                                                               args.steps * STEPS_PER_BENCH, check=False)
             el = gdist.max_over_ranks(time.perf_counter() - t0)
             done = gdist.sum_over_ranks(sum(cells[i] * s for i, s in zip(mine, steps)))
-            # the complex64 floor: per shell, |dmu| between FLOOR_CHECKS further
+            # the single-precision floor: per shell, |dmu| between FLOOR_CHECKS further
             # checks of 100 steps each (outside the timed region)
             floors = []
             for k, i in enumerate(mine):
@@ -916,7 +935,8 @@ def run_extra(args):
                                "mu": mus[-1], "dmu_median": float(np.median(d)), "dmu_max": float(np.max(d)),
                                "dmu_median_rel": float(np.median(d) / abs(mus[-1]))})
             med = np.array([f["dmu_median"] for f in floors])
-            line.update(metric="batched ground states: active-cell ITP steps/s (complex64, FP64 norms)",
+            line.update(metric=f"batched ground states: active-cell ITP steps/s ({BATCH_STATES[args.batch_state][2]}, "
+                               "FP64 norms)", dtype=args.batch_state,
                         unit="cell-steps/s", value=done / el, shells=len(shells), n_active_total=int(sum(cells)),
                         converged=int(gdist.sum_over_ranks(sum(conv))), tol_dmu=args.tol,
                         floor={"checks": FLOOR_CHECKS, "every": 100,
@@ -947,6 +967,8 @@ def main():
                          "time the other workloads (one JSON line each)")
     ap.add_argument("--shells", type=int, default=64, help="batch workload: number of shells")
     ap.add_argument("--tol", type=float, default=1e-8, help="batch workload: |dmu| tolerance")
+    ap.add_argument("--batch-state", choices=sorted(BATCH_STATES), default="c64",
+                    help="batch workload: state type (r32: real float, half the bytes of c64)")
     ap.add_argument("--integrators", action="store_true", help="a --quick run also times RKHE3 and RKCK")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident complex64 timing only (for profiling runs)")

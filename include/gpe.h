@@ -111,8 +111,13 @@ enum { GPE_ORDER_ZMAJOR = 0, GPE_ORDER_MORTON = 1 };
  * the RK4 step of gpe_step_real as two launches, stages 0+1 and stages 2+3,
  * each brick recomputing the first stage of a pair on its one-cell face halo
  * so that the middle stage never leaves shared memory (64 instead of 112
- * bytes of compulsory traffic per stored cell in complex64); the other calls
- * run STAGED on such a grid.  All four give bit-identical results. */
+ * bytes of compulsory traffic per stored cell in complex64); it runs the
+ * imaginary-time step of a complex state as one launch, each brick
+ * recomputing the first Euler substep on its one-cell face halo (20 instead
+ * of 40 bytes per stored cell); the other calls run STAGED on such a grid.
+ * All four give bit-identical real-time results; PAIR's imaginary-time step
+ * sums the norm in another order, so its renormalisation factor can differ
+ * from STAGED's in the last bit. */
 enum { GPE_SCHED_STAGED = 0, GPE_SCHED_WAVE = 1, GPE_SCHED_WAVE2 = 2, GPE_SCHED_PAIR = 3 };
 
 /* Grid options.  Brick shape (bx, by, bz) must be one of 8x8x8 (default when
@@ -240,8 +245,8 @@ enum { GPE_LAYOUT_DENSE = 0, GPE_LAYOUT_COMPACT = 1 };
  * real types GPE_R64 / GPE_R32 hold a real-valued wavefunction for
  * imaginary-time work: the imaginary-time step keeps a real wavefunction
  * real, so half the bytes suffice (Sec. II A).  Real states support load,
- * store, copy, remap, gpe_step_imag, gpe_observables and gpe_ground_state;
- * the calls that need complex values (real-time steps, overlaps, batches,
+ * store, copy, remap, gpe_step_imag, gpe_observables, gpe_ground_state and
+ * batches; the calls that need complex values (real-time steps, overlaps,
  * ramp gradients) refuse them with GPE_ERR_ARG.  Load and store use arrays
  * of double / float.  The state keeps a reference to the grid: destroy
  * states before their grid. */
@@ -412,10 +417,10 @@ int gpe_ground_state(gpe_state *st, const gpe_imag_params *p, double tol_dmu,
 
 /* ------------------------------------------------------------------ batches */
 /* Many independent shells in one persistent launch (one launch of each kernel
- * covers every shell of the batch).  The states must share the state type and
- * brick shape; their grids may differ in size, spacing and potential.  The
- * batch copies the states' tables and keeps them alive; destroy the batch
- * before the states' grids. */
+ * covers every shell of the batch).  The states (complex or real) must share
+ * the state type and brick shape; their grids may differ in size, spacing
+ * and potential.  The batch copies the states' tables and keeps them alive;
+ * destroy the batch before the states' grids. */
 int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out);
 
 /* Imaginary-time ground states of every shell of the batch (Sec. II A,

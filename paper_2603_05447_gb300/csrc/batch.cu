@@ -1,6 +1,8 @@
 // batch.cu -- many independent shells in one persistent launch: imaginary-time
 // ground-state solves (Sec. II A, Eqs. (6)-(7), iterated to a tolerance as in
-// Sec. III) for a batch of states whose grids differ in size and shape.
+// Sec. III) for a batch of states whose grids differ in size and shape.  The
+// states are complex or, since the imaginary-time step keeps a real
+// wavefunction real, real (half the bytes).
 //
 // The batch concatenates the shells' brick lists, records and packed arrays
 // into one layout (neighbour ids and packed offsets shifted by each shell's
@@ -33,9 +35,8 @@ struct ShellParams {
     int has_prev;
 };
 
-template <typename R>
+template <typename R, typename CT = typename Cx<R>::T>
 struct BatchArgs {
-    using CT = typename Cx<R>::T;
     CT *psi;
     CT *tmp;
     const R *E;       // exp(-V dt_s/2) per shell, -1 on inactive cells of stored segments
@@ -48,12 +49,13 @@ struct BatchArgs {
 
 __device__ __forceinline__ int shell_of(const BrickRec &r) { return (int)r.pad[0]; }
 
-template <typename R, int BX, int BY, int BZ, int STAGE>
-__global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G)
+// CT: complex (float2 / double2) or real (float / double) values; a real
+// state stays real under the imaginary-time step
+template <typename R, typename CT, int BX, int BY, int BZ, int STAGE>
+__global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R, CT> a, const GridView G)
 {
-    using CT = typename Cx<R>::T;
     constexpr int NW = KernelCfg<R>::NW;
-    auto &ws = warp_space<R, BX, BY, BZ>();
+    auto &ws = warp_space<R, BX, BY, BZ, CT>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * NW;
     for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
@@ -71,13 +73,11 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const bool act = E[i] >= (R)0;
-                o[i].x = c[i].x + q4 * L[i].x;
-                o[i].y = c[i].y + q4 * L[i].y;
+                o[i] = axpy(c[i], q4, L[i]);
                 if (STAGE == 1) {
-                    const R f = act ? E[i] * ((R)1 - hg * (o[i].x * o[i].x + o[i].y * o[i].y)) : (R)0;
-                    o[i].x *= f;
-                    o[i].y *= f;
-                    acc += (double)(o[i].x * o[i].x + o[i].y * o[i].y);
+                    const R f = act ? E[i] * ((R)1 - hg * norm2(o[i])) : (R)0;
+                    o[i] = scale(o[i], f);
+                    acc += (double)norm2(o[i]);
                 } else if (!act) {
                     o[i] = czero<CT>();
                 }
@@ -85,7 +85,7 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R> a, const GridView G
             st4((STAGE == 0 ? a.tmp : a.psi) + idx, o);
         };
         if (STAGE == 0)
-            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.psi, DiagLoad<R>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2, body);
+            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.psi, DiagLoad<R, CT>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2, body);
         else
             brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.tmp, Identity(), ihx2, ihy2, ihz2, body);
         if (STAGE == 1) {
@@ -123,12 +123,7 @@ __global__ void k_batch_apply_scale(CT *psi, const BrickRec *rec, const ShellPar
         const auto sc = (typename RealOf<CT>::T)P.scale;
         int n = 0;
         for (int w = 0; w < 4; ++w) n += __popc(r.m[w]);
-        for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) {
-            CT v = psi[r.off + i];
-            v.x = v.x * sc;
-            v.y = v.y * sc;
-            psi[r.off + i] = v;
-        }
+        for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) psi[r.off + i] = scale(psi[r.off + i], sc);
     }
 }
 
@@ -138,12 +133,11 @@ __global__ void k_batch_reset_scale(ShellParams *sh, int n)
     if (s < n) sh[s].scale = 1.0;
 }
 
-template <typename R, int BX, int BY, int BZ>
-__global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R> a, const GridView G)
+template <typename R, typename CT, int BX, int BY, int BZ>
+__global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R, CT> a, const GridView G)
 {
-    using CT = typename Cx<R>::T;
     constexpr int NW = KernelCfg<R>::NW;
-    auto &ws = warp_space<R, BX, BY, BZ>();
+    auto &ws = warp_space<R, BX, BY, BZ, CT>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * NW;
     for (int64_t b = (int64_t)blockIdx.x * NW + warp; b < G.nb; b += stride) {
@@ -159,12 +153,12 @@ __global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R> a, const GridView G
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!(V[i] < (R)INFINITY)) continue;
-                const R rho = c[i].x * c[i].x + c[i].y * c[i].y;
+                const R rho = norm2(c[i]);
                 acc[0] += (double)rho;
-                acc[1] += (double)((R)(-0.5) * (c[i].x * L[i].x + c[i].y * L[i].y));
+                acc[1] += (double)((R)(-0.5) * dotre(c[i], L[i]));
                 acc[2] += (double)(V[i] * rho);
                 acc[3] += (double)((R)0.5 * g * rho * rho);
-                acc[4] += (isfinite(c[i].x) && isfinite(c[i].y)) ? 0.0 : 1.0;
+                acc[4] += finite_v(c[i]) ? 0.0 : 1.0;
             }
         });
 #pragma unroll
@@ -238,7 +232,8 @@ using namespace gpe;
 struct gpe_batch {
     int n = 0;
     int dtype = 0, shape = 0, device = 0, nsm = 0;
-    size_t elem = 0;
+    size_t elem = 0;   // bytes per value of the state type
+    size_t relem = 0;  // bytes per real of its precision (E and V tables)
     std::vector<gpe_state *> states;
     std::vector<int64_t> brick_base, packed_base;
     int64_t nb = 0, np = 0;
@@ -289,7 +284,8 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
     for (int i = 1; i < n; ++i)
         if (states[i]->dtype != dtype || states[i]->grid->shape != shape)
             return fail(GPE_ERR_ARG, "batch states must share dtype and brick shape (state %d differs)", i);
-    if (dtype != GPE_C128 && dtype != GPE_C64) return fail(GPE_ERR_ARG, "batches hold complex states");
+    if (dtype != GPE_C128 && dtype != GPE_C64 && dtype != GPE_R64 && dtype != GPE_R32)
+        return fail(GPE_ERR_ARG, "unknown state type %d", dtype);
     for (int i = 0; i < n; ++i)
         if (states[i]->grid->stencil != 7) return fail(GPE_ERR_ARG, "batches run the 7-point stencil (state %d)", i);
     gpe_batch *B = new gpe_batch();
@@ -297,6 +293,7 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
     B->dtype = dtype;
     B->shape = shape;
     B->elem = states[0]->elem;
+    B->relem = (dtype == GPE_C128 || dtype == GPE_R64) ? sizeof(double) : sizeof(float);
     B->states.assign(states, states + n);
     B->device = states[0]->grid->device;
     B->nsm = states[0]->grid->nsm;
@@ -323,8 +320,8 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
     BT(dev_alloc_t(&B->d_rec7, B->nb * 7));
     BT(dev_alloc(&B->d_psi, B->np * B->elem));
     BT(dev_alloc(&B->d_tmp, B->np * B->elem));
-    BT(dev_alloc(&B->d_E, B->np * B->elem / 2));
-    BT(dev_alloc(&B->d_Vr, B->np * B->elem / 2));
+    BT(dev_alloc(&B->d_E, B->np * B->relem));
+    BT(dev_alloc(&B->d_Vr, B->np * B->relem));
     BT(dev_alloc_t(&B->d_V, B->np));
     BT(dev_alloc_t(&B->d_sh, n));
     BT(dev_alloc_t(&B->d_part, B->nb * 5));
@@ -359,7 +356,7 @@ extern "C" int gpe_batch_create(gpe_state *const *states, int n, gpe_batch **out
         cudaMemcpy(B->d_bb, B->brick_base.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(B->d_tmp, 0, B->np * B->elem) != cudaSuccess)
         BT(fail(GPE_ERR_CUDA, "batch table upload failed"));
-    if (dtype == GPE_C128) k_d2r<double><<<B->nsm * 8, 256>>>(B->d_V, (double *)B->d_Vr, B->np);
+    if (B->relem == sizeof(double)) k_d2r<double><<<B->nsm * 8, 256>>>(B->d_V, (double *)B->d_Vr, B->np);
     else k_d2r<float><<<B->nsm * 8, 256>>>(B->d_V, (float *)B->d_Vr, B->np);
     count_launch();
     if (cudaDeviceSynchronize() != cudaSuccess) BT(fail(GPE_ERR_CUDA, "batch setup kernel failed"));
@@ -380,11 +377,10 @@ extern "C" int gpe_batch_destroy(gpe_batch *B)
 
 namespace gpe {
 
-template <typename R, int BX, int BY, int BZ>
+template <typename R, typename CT, int BX, int BY, int BZ>
 static int batch_record_block(gpe_batch *B, int64_t nsteps, cudaStream_t s)
 {
-    using CT = typename Cx<R>::T;
-    BatchArgs<R> a;
+    BatchArgs<R, CT> a;
     a.psi = (CT *)B->d_psi;
     a.tmp = (CT *)B->d_tmp;
     a.E = (const R *)B->d_E;
@@ -394,11 +390,11 @@ static int batch_record_block(gpe_batch *B, int64_t nsteps, cudaStream_t s)
     a.brick_base = B->d_bb;
     a.n = B->n;
     const GridView G{B->d_nbr, B->d_rec, B->d_rec7, B->nb};
-    auto ka = k_batch_itp<R, BX, BY, BZ, 0>;
-    auto kb = k_batch_itp<R, BX, BY, BZ, 1>;
-    auto ko = k_batch_obs<R, BX, BY, BZ>;
+    auto ka = k_batch_itp<R, CT, BX, BY, BZ, 0>;
+    auto kb = k_batch_itp<R, CT, BX, BY, BZ, 1>;
+    auto ko = k_batch_obs<R, CT, BX, BY, BZ>;
     const int th = KernelCfg<R>::THREADS;
-    const size_t smem = smem_bytes<R, BX, BY, BZ>();
+    const size_t smem = smem_bytes<R, BX, BY, BZ, CT>();
     const int per = std::min(prepare_kernel(ka, th, smem), std::min(prepare_kernel(kb, th, smem), prepare_kernel(ko, th, smem)));
     const int64_t need = (B->nb + KernelCfg<R>::NW - 1) / KernelCfg<R>::NW;
     const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->nsm * per, need));
@@ -426,9 +422,15 @@ static int batch_record_block(gpe_batch *B, int64_t nsteps, cudaStream_t s)
 
 static int batch_record(gpe_batch *B, int64_t nsteps, cudaStream_t s)
 {
-    const bool c128 = B->dtype == GPE_C128;
-#define BATCH_CASE(id, X, Y, Z) \
-    case id: return c128 ? batch_record_block<double, X, Y, Z>(B, nsteps, s) : batch_record_block<float, X, Y, Z>(B, nsteps, s);
+#define BATCH_CASE(id, X, Y, Z)                                                              \
+    case id:                                                                                 \
+        switch (B->dtype) {                                                                  \
+        case GPE_C128: return batch_record_block<double, double2, X, Y, Z>(B, nsteps, s);    \
+        case GPE_C64: return batch_record_block<float, float2, X, Y, Z>(B, nsteps, s);       \
+        case GPE_R64: return batch_record_block<double, double, X, Y, Z>(B, nsteps, s);      \
+        case GPE_R32: return batch_record_block<float, float, X, Y, Z>(B, nsteps, s);        \
+        }                                                                                    \
+        break;
     switch (B->shape) { GPE_SHAPES(BATCH_CASE) }
 #undef BATCH_CASE
     return fail(GPE_ERR_STATE, "bad brick shape");
@@ -480,7 +482,7 @@ extern "C" int gpe_batch_ground_state(gpe_batch *B, const gpe_imag_params *per_s
         GPE_TRY_CUDA(cudaMemcpyAsync((char *)B->d_psi + B->packed_base[i] * B->elem, B->states[i]->d_psi,
                                      B->states[i]->grid->n_packed * B->elem, cudaMemcpyDeviceToDevice, s));
     GPE_TRY_CUDA(cudaStreamSynchronize(s));
-    GPE_TRY(B->dtype == GPE_C128 ? batch_make_E<double>(B) : batch_make_E<float>(B));
+    GPE_TRY(B->relem == sizeof(double) ? batch_make_E<double>(B) : batch_make_E<float>(B));
     GPE_TRY_CUDA(cudaDeviceSynchronize());
     // one graph per (block length) replayed until every shell converged
     const uint64_t key = (uint64_t)check_every;

@@ -27,8 +27,8 @@ __global__ void k_make_E(const double *V, R *E, int64_t n, double dt)
 // Stage B gathers tmp, takes the second Euler substep, applies the diagonal
 // half step again, writes psi and sums |psi|^2 in FP64; the factor
 // sqrt(N / (sum |psi|^2 dV)) is stored for the next step's stage A (or the
-// end of the call).  E = 0 on inactive cells of stored segments (V = +inf),
-// so those stay zero.
+// end of the call).  E = -1 marks the inactive cells of stored segments
+// (V = +inf), which are set to zero.
 template <typename R, typename CT = typename Cx<R>::T>
 struct ItpArgs {
     CT *psi;

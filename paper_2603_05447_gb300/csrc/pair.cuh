@@ -132,11 +132,23 @@ __device__ __forceinline__ void seg_unit_async(void *dst, const BrickRec &r, int
     cp_async16(dst, reinterpret_cast<const char *>(src + (ok ? j : 0u)) + 16 * k, ok);
 }
 
+// A fill hook stages per-cell data of the same cells beside u (the
+// imaginary-time pass stages the propagator table E): own(slot, stored, j)
+// for each of the brick's segments, seg(slot, r, q) for each halo segment
+// (segment q of the brick with record r) and xh(side, row, r, q) for each x
+// halo row.  The RK4 passes use none.
+struct NoFillHook {
+    __device__ __forceinline__ void own(int, bool, uint32_t) const {}
+    __device__ __forceinline__ void seg(int, const BrickRec &, int) const {}
+    __device__ __forceinline__ void xh(int, int, const BrickRec &, int) const {}
+};
+
 // Stage u of brick b: records, the own stored segments, the two-deep y and z
 // face layers, the one-deep y-z edge rows and the x halo cells of every row
 // with y in [-1, BY], z in [-1, BZ] (no y-z corner rows).
-template <typename CT, int BX, int BY, int BZ>
-__device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const PairView &P, int64_t b, const CT *src)
+template <typename CT, int BX, int BY, int BZ, typename HOOK = NoFillHook>
+__device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const PairView &P, int64_t b, const CT *src,
+                                          const HOOK &hook = HOOK())
 {
     using PS = PairSpace<CT, BX, BY, BZ>;
     constexpr int SX = PS::SX, PL = PS::PLANE_B, UPS = PS::UPS, NXU = PS::NXU;
@@ -167,9 +179,11 @@ __device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const P
             const char *g = reinterpret_cast<const char *>(src + R0.off + 4u * rank);
 #pragma unroll
             for (int k = 0; k < UPS; ++k) cp_async16(&ps.u[k][sl], g + 16 * k, true);
+            hook.own(sl, true, R0.off + 4u * rank);
         } else {
 #pragma unroll
             for (int k = 0; k < UPS; ++k) ps.u[k][sl] = make_uint4(0, 0, 0, 0);
+            hook.own(sl, false, 0u);
         }
     }
     if (t == 0) ps.nst = __popc(R0.m[0]) + __popc(R0.m[1]) + __popc(R0.m[2]) + __popc(R0.m[3]);
@@ -181,6 +195,7 @@ __device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const P
         const int z = pz < 2 ? pz - 2 : BZ + (pz - 2);
         const int zs = pz < 2 ? BZ - 2 + pz : pz - 2;
         seg_unit_async(&ps.u[k][PS::slot(hx, y, z)], ps.rec[pz < 2 ? 5 : 6], hx + SX * y + PL * zs, k, src);
+        if (k == 0) hook.seg(PS::slot(hx, y, z), ps.rec[pz < 2 ? 5 : 6], hx + SX * y + PL * zs);
     }
     // y face layers: rows -2, -1 (rows BY-2, BY-1 of the -y brick), BY, BY+1
     // (rows 0, 1 of the +y brick); z in [0, BZ)
@@ -190,6 +205,7 @@ __device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const P
         const int y = py < 2 ? py - 2 : BY + (py - 2);
         const int ys = py < 2 ? BY - 2 + py : py - 2;
         seg_unit_async(&ps.u[k][PS::slot(hx, y, z)], ps.rec[py < 2 ? 3 : 4], hx + SX * ys + PL * z, k, src);
+        if (k == 0) hook.seg(PS::slot(hx, y, z), ps.rec[py < 2 ? 3 : 4], hx + SX * ys + PL * z);
     }
     // y-z edge rows (y, z) in {-1, BY} x {-1, BZ}: records 15-18 are the edge
     // neighbours (0,-1,-1) (0,+1,-1) (0,-1,+1) (0,+1,+1)
@@ -198,6 +214,9 @@ __device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const P
         const bool yp = e & 1, zp = e & 2;
         seg_unit_async(&ps.u[k][PS::slot(hx, yp ? BY : -1, zp ? BZ : -1)], ps.rec[15 + e],
                        hx + SX * (yp ? 0 : BY - 1) + PL * (zp ? 0 : BZ - 1), k, src);
+        if (k == 0)
+            hook.seg(PS::slot(hx, yp ? BY : -1, zp ? BZ : -1), ps.rec[15 + e],
+                     hx + SX * (yp ? 0 : BY - 1) + PL * (zp ? 0 : BZ - 1));
     }
     // x halo cells: rows with y in [-1, BY], z in [-1, BZ] except the four y-z
     // corners; the -x side takes cells 2, 3 of the source's last segment of the
@@ -222,6 +241,7 @@ __device__ __forceinline__ void pair_fill(PairSpace<CT, BX, BY, BZ> &ps, const P
         const int q = (side == 0 ? SX - 1 : 0) + SX * ys + PL * zs;
         CT *dst = side == 0 ? &ps.uxl[PS::row(y, z)][k * (2 / NXU)] : &ps.uxr[PS::row(y, z)][k * (2 / NXU)];
         seg_unit_async(dst, ps.rec[rec], q, side == 0 ? UPS - NXU + k : k, src);
+        if (k == 0) hook.xh(side, PS::row(y, z), ps.rec[rec], q);
     }
 }
 

@@ -30,6 +30,7 @@
 
 #include "gpe_internal.cuh"
 #include "kernels.cuh"
+#include "itp_pair.cuh"
 #include "pair.cuh"
 
 namespace gpe {
@@ -1151,6 +1152,43 @@ static int itp_run(gpe_state *st, const gpe_imag_params *p, int64_t nsteps, cuda
             GPE_LAUNCH_CHECK();
             advance_wave(st, 2, nblk, true);
         }
+        k_apply_scale<CT><<<g->nsm * 8, 256, 0, s>>>((CT *)st->d_psi, g->n_packed, st->red.scalars);
+        GPE_LAUNCH_CHECK();
+        return GPE_OK;
+    }
+    if constexpr (is_cplx<CT>()) if (g->sched == GPE_SCHED_PAIR) {
+        // one pass per step; the state alternates between the psi buffer and
+        // work buffer 0
+        GPE_TRY(ensure_nbr18(const_cast<gpe_grid *>(g)));
+        const PairView P{g->d_rec, g->d_nbr18, g->nb};
+        auto k = k_itp_fused<R, BX, BY, BZ>;
+        const size_t psm = sizeof(ItpPairSpace<CT, BX, BY, BZ>);
+        const int64_t res = (int64_t)g->nsm * per_sm_for(k, PAIR_THREADS, psm);
+        const int nbk = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(g->nb, res), st->red.max_blocks));
+        CT *bufA = (CT *)st->d_psi, *bufB = (CT *)st->d_work[0];
+        // cnt steps from bufA; after an odd count psi is copied back to bufA
+        auto record = [&](cudaStream_t cs, int64_t cnt) -> int {
+            for (int64_t n = 0; n < cnt; ++n) {
+                ItpArgs<R, CT> an = a;
+                an.psi = (n % 2 == 0) ? bufA : bufB;
+                an.tmp = (n % 2 == 0) ? bufB : bufA;
+                k<<<nbk, PAIR_THREADS, psm, cs>>>(an, P, st->red.partials, st->red.counter);
+                GPE_LAUNCH_CHECK();
+            }
+            if (cnt % 2)
+                GPE_TRY_CUDA(cudaMemcpyAsync(bufA, bufB, (size_t)g->n_packed * sizeof(CT), cudaMemcpyDeviceToDevice, cs));
+            return GPE_OK;
+        };
+        int64_t left = nsteps;
+        if (use_graph(st, s, nsteps)) {
+            const int G_ = st->graph_steps;
+            uint64_t key = fnv1a(p, sizeof *p);
+            key = fnv1a(&G_, sizeof G_, key);
+            key = fnv1a(&a.E, sizeof a.E, key);
+            GPE_TRY(replay_graph(st, 1, key, G_, nsteps / G_, s, [&](cudaStream_t cs) { return record(cs, G_); }));
+            left = nsteps % G_;
+        }
+        GPE_TRY(record(s, left));
         k_apply_scale<CT><<<g->nsm * 8, 256, 0, s>>>((CT *)st->d_psi, g->n_packed, st->red.scalars);
         GPE_LAUNCH_CHECK();
         return GPE_OK;

@@ -108,6 +108,60 @@ def test_batch_convergence_matches_single_state_solver(dtype):
             gpe.gpe_grid_destroy(g)
 
 
+@pytest.mark.parametrize("real,cplx", [(gpe.GPE_R64, gpe.GPE_C128), (gpe.GPE_R32, gpe.GPE_C64)])
+def test_batch_of_real_states_matches_the_complex_batch_and_the_solo_solver(real, cplx):
+    """A real starting state stays real under the imaginary-time step, so a
+    batch of real states runs the complex batch's arithmetic on the real parts
+    (the imaginary parts stay exactly zero): same stopping checks, same
+    wavefunctions and chemical potentials.  Each shell also matches the
+    single-state solver on the same real state."""
+    cases = trap_cases()
+    rnp = {gpe.GPE_R64: np.float64, gpe.GPE_R32: np.float32}[real]
+    cnp = {gpe.GPE_C128: np.complex128, gpe.GPE_C64: np.complex64}[cplx]
+
+    def made(dtype, npt):
+        out = []
+        for c in cases:
+            grid = gpe.gpe_grid_create_dense(c.gbox, c.V, c.V_cut, gpe.make_opts((8, 8, 4)))
+            st = gpe.gpe_state_create(grid, dtype)
+            gpe.gpe_state_load(st, np.ascontiguousarray(np.abs(c.psi).astype(npt)), gpe.GPE_LAYOUT_DENSE)
+            out.append((grid, st))
+        return out
+
+    def store(c, st, npt):
+        out = np.zeros(c.box.shape, npt)
+        gpe.gpe_state_store(st, out, gpe.GPE_LAYOUT_DENSE)
+        return out.astype(np.complex128)
+
+    R, C, solo = made(real, rnp), made(cplx, cnp), made(real, rnp)
+    br = gpe.gpe_batch_create([st for _, st in R])
+    bc = gpe.gpe_batch_create([st for _, st in C])
+    try:
+        params = [gpe.gpe_imag_params(c.g, c.dt, 1.0) for c in cases]
+        tol = 1e-7 if real == gpe.GPE_R64 else 1e-5
+        rc_r, conv_r, steps_r, obs_r = gpe.gpe_batch_ground_state(br, params, tol, 50, 20000)
+        rc_c, conv_c, steps_c, obs_c = gpe.gpe_batch_ground_state(bc, params, tol, 50, 20000)
+        assert rc_r == rc_c == gpe.GPE_OK and all(conv_r) and conv_r == conv_c
+        assert steps_r == steps_c and len(set(steps_r)) > 1
+        for c, (_, sr), (_, sc), (_, s1), n, orr, oc, p in zip(cases, R, C, solo, steps_r, obs_r, obs_c, params):
+            a, b = store(c, sr, rnp), store(c, sc, cnp)
+            assert np.abs(b.imag).max() == 0.0
+            assert rel_l2(a, b) <= 1e-15
+            for k in ("norm", "energy", "mu", "e_kin", "e_pot", "e_int"):
+                assert abs(orr[k] - oc[k]) <= 1e-14 * max(1.0, abs(oc[k])), k
+            n1, o1 = gpe.gpe_ground_state(s1, p, tol, 50, 20000)
+            assert n1 == n
+            tol_mu = 1e-10 if real == gpe.GPE_R64 else 1e-6
+            assert abs(orr["mu"] - o1["mu"]) <= tol_mu * abs(o1["mu"])
+            assert rel_l2(a, store(c, s1, rnp)) <= (1e-10 if real == gpe.GPE_R64 else 1e-5)
+    finally:
+        gpe.gpe_batch_destroy(br)
+        gpe.gpe_batch_destroy(bc)
+        for g, st in R + C + solo:
+            gpe.gpe_state_destroy(st)
+            gpe.gpe_grid_destroy(g)
+
+
 def test_graph_replay_matches_eager_steps_bit_for_bit():
     case = ragged_shell()
     g1, eager = make(case)

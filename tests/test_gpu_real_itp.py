@@ -126,8 +126,7 @@ def test_complex_only_calls_refuse_real_states():
     A, B = State(case, gpe.GPE_R64), State(case, gpe.GPE_R64)
     try:
         for call in (lambda: gpe.gpe_step_real(A.st, gpe.real_params(case.g, case.dt), 1),
-                     lambda: gpe.gpe_overlap(A.st, B.st),
-                     lambda: gpe.gpe_batch_create([A.st, B.st])):
+                     lambda: gpe.gpe_overlap(A.st, B.st)):
             with pytest.raises(gpe.GpeError) as e:
                 call()
             assert e.value.code == gpe.GPE_ERR_ARG
