@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "gpe_internal.cuh"
+#include "kernels.cuh"
 #include "stencil.cuh"
 
 namespace gpe {
@@ -66,10 +67,11 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R, CT> a, const GridVi
         const R ihx2 = (R)P.ihx2, ihy2 = (R)P.ihy2, ihz2 = (R)P.ihz2;
         const R q4 = dt / (R)4, hg = g * dt / (R)2;
         double acc = 0.0;
-        auto body = [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
-            R E[4];
-            ldr4(a.E + idx, E);
+        // E of each segment is loaded ahead (while the tile is in flight)
+        auto body = [&](uint32_t idx, const typename ELoad<R>::P &p, const CT(&c)[4], const CT(&L)[4]) {
+            const R(&E)[4] = p.e;
             CT o[4];
+            R n4 = (R)0;  // the segment's |psi|^2, added to the FP64 sum once
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const bool act = E[i] >= (R)0;
@@ -77,17 +79,19 @@ __global__ void GPE_BOUNDS(R) k_batch_itp(const BatchArgs<R, CT> a, const GridVi
                 if (STAGE == 1) {
                     const R f = act ? E[i] * ((R)1 - hg * norm2(o[i])) : (R)0;
                     o[i] = scale(o[i], f);
-                    acc += (double)norm2(o[i]);
+                    n4 = add_rn(n4, norm2(o[i]));
                 } else if (!act) {
                     o[i] = czero<CT>();
                 }
             }
+            if (STAGE == 1) acc += (double)n4;
             st4((STAGE == 0 ? a.tmp : a.psi) + idx, o);
         };
         if (STAGE == 0)
-            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.psi, DiagLoad<R, CT>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2, body);
+            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.psi, DiagLoad<R, CT>{(R)P.scale, hg, a.E}, ihx2, ihy2, ihz2,
+                                           ELoad<R>{a.E}, body);
         else
-            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.tmp, Identity(), ihx2, ihy2, ihz2, body);
+            brick_apply<BX, BY, BZ, false>(ws, G, b, nx, a.tmp, Identity(), ihx2, ihy2, ihz2, ELoad<R>{a.E}, body);
         if (STAGE == 1) {
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
             if (lane == 0) a.part[b * 5] = acc;
@@ -150,16 +154,21 @@ __global__ void GPE_BOUNDS(R) k_batch_obs(const BatchArgs<R, CT> a, const GridVi
                                        [&](uint32_t idx, const CT(&c)[4], const CT(&L)[4]) {
             R V[4];
             ldr4(a.V + idx, V);
+            R t[4] = {(R)0, (R)0, (R)0, (R)0};  // the segment's terms, added to the FP64 sums once
+            int nf = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!(V[i] < (R)INFINITY)) continue;
                 const R rho = norm2(c[i]);
-                acc[0] += (double)rho;
-                acc[1] += (double)((R)(-0.5) * dotre(c[i], L[i]));
-                acc[2] += (double)(V[i] * rho);
-                acc[3] += (double)((R)0.5 * g * rho * rho);
-                acc[4] += finite_v(c[i]) ? 0.0 : 1.0;
+                t[0] = add_rn(t[0], rho);
+                t[1] = add_rn(t[1], (R)(-0.5) * dotre(c[i], L[i]));
+                t[2] = add_rn(t[2], V[i] * rho);
+                t[3] = add_rn(t[3], (R)0.5 * g * rho * rho);
+                nf += finite_v(c[i]) ? 0 : 1;
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += (double)t[k];
+            acc[4] += (double)nf;
         });
 #pragma unroll
         for (int k = 0; k < 5; ++k) {

@@ -216,6 +216,7 @@ __device__ __forceinline__ void itp_pair_brick(ItpPairSpace<typename Cx<R>::T, B
         const int hx = q % SX, y = (q / SX) % BY, z = q / PL;
         CT c[4], L[4], o[4];
         R e4[4];
+        R n4 = (R)0;  // the segment's |psi|^2, added to the FP64 sum once
         pair_lap_v(ps, hx, y, z, c, L, a.ihx2, a.ihy2, a.ihz2, c6);
         sp.eget(PS::slot(hx, y, z), e4);
 #pragma unroll
@@ -223,8 +224,9 @@ __device__ __forceinline__ void itp_pair_brick(ItpPairSpace<typename Cx<R>::T, B
             o[k] = axpy(c[k], q4, L[k]);
             const R f = e4[k] >= (R)0 ? e4[k] * ((R)1 - hg * norm2(o[k])) : (R)0;
             o[k] = scale(o[k], f);
-            acc += (double)norm2(o[k]);
+            n4 = add_rn(n4, norm2(o[k]));
         }
+        acc += (double)n4;
         st4(a.tmp + R0.off + 4u * (uint32_t)i, o);
     }
     __syncthreads();  // the tiles are reused for the next brick

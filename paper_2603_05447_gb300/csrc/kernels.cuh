@@ -8,6 +8,11 @@
 
 namespace gpe {
 
+// a + b rounded once and never fused with the product that feeds it, so that
+// the per-segment sums of a real state and of a complex state with zero
+// imaginary part round identically
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
 // E = exp(-V dt/2) in the state precision (Eq. (7): the diagonal propagator
 // is precomputed once per dt); E = -1 marks the inactive cells of stored
@@ -82,13 +87,15 @@ __device__ __forceinline__ void itp_brick_b(const ItpArgs<R, CT> &a, const GridV
     brick_apply<BX, BY, BZ, CG>(ws, G, b, next, a.tmp, Identity(), a.ihx2, a.ihy2, a.ihz2, ELoad<R>{a.E},
                                 [&](uint32_t idx, const typename ELoad<R>::P &p, const CT(&c)[4], const CT(&L)[4]) {
         CT o[4];
+        R n4 = (R)0;  // the segment's |psi|^2, added to the FP64 sum once
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             o[i] = axpy(c[i], q4, L[i]);
             const R f = p.e[i] >= (R)0 ? p.e[i] * ((R)1 - hg * norm2(o[i])) : (R)0;
             o[i] = scale(o[i], f);
-            acc += (double)norm2(o[i]);
+            n4 = add_rn(n4, norm2(o[i]));
         }
+        acc += (double)n4;
         st4(a.psi + idx, o);
     });
 }
@@ -166,17 +173,24 @@ __global__ void GPE_BOUNDS_NP(R) k_obs(const ObsArgs<R, CT> a, const GridView G)
             R V0[4], V1[4];
             ldr4(a.V0 + idx, V0);
             if (a.V1) ldr4(a.V1 + idx, V1);
+            // the segment's four terms summed in the state precision, then
+            // added to the FP64 sums once (one FP64 add per segment and term)
+            R t[4] = {(R)0, (R)0, (R)0, (R)0};
+            int nf = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!(V0[i] < (R)INFINITY)) continue;
                 const R V = a.V1 ? ((R)1 - a.s) * V0[i] + a.s * V1[i] : V0[i];
                 const R rho = norm2(c[i]);
-                acc[0] += (double)rho;
-                acc[1] += (double)((R)(-0.5) * dotre(c[i], L[i]));
-                acc[2] += (double)(V * rho);
-                acc[3] += (double)((R)0.5 * a.g * rho * rho);
-                acc[4] += finite_v(c[i]) ? 0.0 : 1.0;
+                t[0] = add_rn(t[0], rho);
+                t[1] = add_rn(t[1], (R)(-0.5) * dotre(c[i], L[i]));
+                t[2] = add_rn(t[2], V * rho);
+                t[3] = add_rn(t[3], (R)0.5 * a.g * rho * rho);
+                nf += finite_v(c[i]) ? 0 : 1;
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += (double)t[k];
+            acc[4] += (double)nf;
         });
     }
     double tot[5];
