@@ -86,6 +86,7 @@ __global__ void GPE_BOUNDS(R) k_adj_stage(const AdjArgs<R> a, const GridView G)
             ld4<false>(a.lam + idx, lam);
             if (!a.first) ld4<false>(a.acc + idx, acc);
             CT nacc[4], mo[4];
+            R d4 = (R)0;  // the segment's share of the knot derivative, added in FP64 once
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!(V0[i] < (R)INFINITY)) {  // inactive cell of a stored segment
@@ -106,13 +107,14 @@ __global__ void GPE_BOUNDS(R) k_adj_stage(const AdjArgs<R> a, const GridView G)
                 CT nu;
                 nu.x = -ci;
                 nu.y = cr;
-                if (BLEND) dot[0] += (double)(dV * (M[i].x * Y[i].y - M[i].y * Y[i].x));
+                if (BLEND) d4 += dV * (M[i].x * Y[i].y - M[i].y * Y[i].x);
                 const CT base = a.first ? lam[i] : acc[i];
                 nacc[i].x = base.x + nu.x;
                 nacc[i].y = base.y + nu.y;
                 mo[i].x = a.cl * lam[i].x + a.cn * nu.x;
                 mo[i].y = a.cl * lam[i].y + a.cn * nu.y;
             }
+            if (BLEND) dot[0] += (double)d4;
             if (a.last) {
                 st4(a.lam_out + idx, nacc);
             } else {
