@@ -709,7 +709,7 @@ def roi_sweep(gpe, inputs, torch):
 
 def ramp_traced(gpe, inputs, torch, nsteps=5000, every=500, n_overlap=5, nsteps_overlap=4000):
     """The hollowing ramp of the 2048^3 box tracked over a run of `nsteps` RK4
-    steps (the configuration names 5e4; a tenth is run): norm and energy
+    steps (the configuration names 5e4; 5000 by default): norm and energy
     every `every` steps through gpe_step_real_traced.  The overlap with the
     instantaneous ground state needs a ground-state solve of V(s(t)) per
     trace point, so it is tracked on the 512^3 version of the same ramp:
@@ -818,7 +818,7 @@ def run_extra(args):
         elif args.workload == "stages512":
             line.update(stages_run(gpe, inputs, torch))
         elif args.workload == "ramp_traced":
-            line.update(ramp_traced(gpe, inputs, torch))
+            line.update(ramp_traced(gpe, inputs, torch, nsteps=args.ramp_steps, every=max(1, args.ramp_steps // 10)))
         elif args.workload in ("ramp2048", "adjoint512"):
             rw = inputs.RAMP_2048 if args.workload == "ramp2048" else inputs.RAMP_512
             grid = _ramp_grid(gpe, rw)
@@ -967,6 +967,8 @@ def main():
                          "time the other workloads (one JSON line each)")
     ap.add_argument("--shells", type=int, default=64, help="batch workload: number of shells")
     ap.add_argument("--tol", type=float, default=1e-8, help="batch workload: |dmu| tolerance")
+    ap.add_argument("--ramp-steps", type=int, default=5000,
+                    help="ramp_traced workload: RK4 steps of the tracked 2048^3 ramp (the configuration names 5e4)")
     ap.add_argument("--batch-state", choices=sorted(BATCH_STATES), default="c64",
                     help="batch workload: state type (r32: real float, half the bytes of c64)")
     ap.add_argument("--integrators", action="store_true", help="a --quick run also times RKHE3 and RKCK")

@@ -195,3 +195,50 @@ def test_rk4_19_point_full_size_sampled(big):
         c = np.flatnonzero(np.all(g.ijk() == HALF, axis=1))[0]
         scale = np.max(np.abs(before[idx[m]]))
         assert abs(after[idx[HALF, HALF, HALF]] - y[c]) <= tol * scale, (i, j, k)
+
+
+def test_pair_schedule_full_size_sampled(big):
+    """The fused-pair schedule on the same shell (its grid packs the cells as
+    the staged grid does): one RK4 step in two fused launches is bit-identical
+    to the staged step on every cell; one imaginary-time step in one launch
+    matches the oracle on the samples up to one common factor."""
+    wl, tol = big["wl"], 2e-6
+    b = wl.box
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    grid = gpe.gpe_grid_create_analytic(gpe.make_box(b.nx, b.ny, b.nz, b.hx), pot, wl.V_cut,
+                                        gpe.make_opts(big["shape"], sched=gpe.GPE_SCHED_PAIR))
+    try:
+        assert gpe.gpe_grid_get_info(grid).n_packed == big["info"].n_packed
+        st = gpe.gpe_state_create(grid, gpe.GPE_C64)
+        before = np.ascontiguousarray(big["psi0"].astype(np.complex64))
+        try:
+            gpe.gpe_state_load(st, before, gpe.GPE_LAYOUT_COMPACT)
+            gpe.gpe_step_real(st, gpe.real_params(wl.g, wl.stable_dt()), 1)
+            rk = np.zeros_like(before)
+            gpe.gpe_state_store(st, rk, gpe.GPE_LAYOUT_COMPACT)
+            gpe.gpe_state_load(st, before, gpe.GPE_LAYOUT_COMPACT)
+            gpe.gpe_step_imag(st, gpe.gpe_imag_params(wl.g, wl.stable_dt(), 1.0), 1)
+            it = np.zeros_like(before)
+            gpe.gpe_state_store(st, it, gpe.GPE_LAYOUT_COMPACT)
+        finally:
+            gpe.gpe_state_destroy(st)
+    finally:
+        gpe.gpe_grid_destroy(grid)
+    _, rk_staged = run(big, gpe.GPE_C64, "rk4")
+    assert np.array_equal(rk.astype(np.complex128), rk_staged)
+    before, it = before.astype(np.complex128), it.astype(np.complex128)
+    got, ref, scl = [], [], []
+    for (i, j, k) in samples(big, 14):
+        m, idx, Vh = patch(big, i, j, k)
+        g = oracle.Grid(m, wl.box.hx)
+        y, nrm = oracle.itp_step(g, Vh[m], before[idx[m]], wl.g, wl.stable_dt(), 1.0)
+        y = y / math.sqrt(1.0 / nrm)
+        c = np.flatnonzero(np.all(g.ijk() == HALF, axis=1))[0]
+        ref.append(y[c])
+        got.append(it[idx[HALF, HALF, HALF]])
+        scl.append(np.max(np.abs(before[idx[m]])))
+    got, ref, scl = np.array(got), np.array(ref), np.array(scl)
+    big_ = np.abs(ref) > 1e-3 * scl
+    factor = np.median(np.real(got[big_] / ref[big_]))
+    assert 0.9 < factor < 1.1
+    assert np.all(np.abs(got - factor * ref) <= tol * scl * factor)
