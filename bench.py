@@ -595,6 +595,38 @@ def _core_state(gpe, inputs, rw, grid, dtype):
     return np.ascontiguousarray(out.astype(np.complex64 if dtype == gpe.GPE_C64 else np.complex128))
 
 
+def _final_shell_ground_state(gpe, rw, dst):
+    """The imaginary-time ground state of the ramp's final potential (the
+    shell alone): solved on its own grid (region V1 < 5 mu_TF, Thomas-Fermi
+    start, complex64, |dmu| < 1e-7 mu), then remapped onto dst's grid (the
+    ramp's union region).  Returns what the solve reported."""
+    b = rw.shell.box
+    gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, rw.shell.w, *rw.shell.axes)
+    mu = gpe.gpe_tf_mu_analytic(gb, pot, rw.shell.g, rw.shell.N)
+    g1 = gpe.gpe_grid_create_analytic(gb, pot, 5.0 * mu, gpe.make_opts((8, 8, 4)))
+    s1 = gpe.gpe_state_create(g1, gpe.GPE_C64)
+    try:
+        idx, i, j, k = gpe.packed_coords(g1)
+        psi = np.zeros(gpe.gpe_grid_get_info(g1).n_packed, np.complex64)
+        psi[idx] = np.sqrt(np.maximum(mu - rw.shell.potential(b.x0 + i * b.hx, b.y0 + j * b.hy, b.z0 + k * b.hz),
+                                      0.0) / rw.shell.g)
+        gpe.gpe_state_load(s1, psi, gpe.GPE_LAYOUT_COMPACT)
+        dti = min(0.5 * rw.shell.h ** 2, 0.5 / mu)
+        try:
+            n, o = gpe.gpe_ground_state(s1, gpe.gpe_imag_params(rw.shell.g, dti, rw.shell.N), 1e-7 * mu, 100, 20000)
+            conv = True
+        except gpe.GpeError:
+            n, o, conv = 20000, gpe.gpe_observables(s1, rw.shell.g), False
+        gpe.gpe_state_remap(dst, s1)
+        kept = gpe.gpe_observables(dst, rw.shell.g, 1.0)["norm"]
+        return {"steps": n, "converged": conv, "mu": o["mu"], "n_active": gpe.gpe_grid_get_info(g1).n_active,
+                "norm_on_ramp_grid": kept}
+    finally:
+        gpe.gpe_state_destroy(s1)
+        gpe.gpe_grid_destroy(g1)
+
+
 def stages_run(gpe, inputs, torch, n_stages=66, steps_per_stage=20):
     """Multi-stage ramp (Sec. V) on a 512^3 shell: 67 dense FP32 potentials
     on the device, evenly spaced blends of the shell and a softer, slightly
@@ -869,8 +901,13 @@ def run_extra(args):
                             config="2048^3 box, shell semi-axis 800 cells + harmonic core radius 0.24, g=5000, "
                                    "16 seeded monotone knots over the run")
             else:
+                # the target: the imaginary-time ground state of the final shell
                 tg = gpe.gpe_state_create(grid, gpe.GPE_C64)
-                gpe.gpe_state_copy(tg, st)
+                target = _final_shell_ground_state(gpe, rw, tg)
+                # a second target the run's state still overlaps: the initial
+                # core (the shell's ground state vanishes where the core is)
+                tg0 = gpe.gpe_state_create(grid, gpe.GPE_C64)
+                gpe.gpe_state_copy(tg0, st)
                 nsteps = 4000
                 K = 64
                 p = gpe.real_params(rw.shell.g, dt, gpe.GPE_V_BLEND, knots, nsteps * dt)
@@ -881,14 +918,18 @@ def run_extra(args):
                 t1 = time.perf_counter()
                 loss, grad = gpe.gpe_ramp_backward(tape, tg, 16)
                 t2 = time.perf_counter()
+                loss0, grad0 = gpe.gpe_ramp_backward(tape, tg0, 16)  # the same tape, untimed
                 gpe.gpe_tape_destroy(tape)
                 gpe.gpe_state_destroy(tg)
+                gpe.gpe_state_destroy(tg0)
                 line.update(metric="adjoint ramp gradient (4000 RK4 steps, K=64, complex64 + FP64 gradient)",
                             unit="s", value=t2 - t0, forward_s=t1 - t0, backward_s=t2 - t1,
                             n_active=info.n_active, loss=loss, grad_norm=float(np.linalg.norm(grad)),
-                            forward_cell_steps_per_s=info.n_active * nsteps / (t1 - t0),
+                            forward_cell_steps_per_s=info.n_active * nsteps / (t1 - t0), target=target,
+                            initial_state_target={"loss": loss0, "grad_norm": float(np.linalg.norm(grad0)),
+                                                  "grad": [float(x) for x in grad0]},
                             config="512^3 box, shell semi-axis 200 cells + harmonic core, ~5e6 active, target = "
-                                   "initial state")
+                                   "imaginary-time ground state of the final shell")
             gpe.gpe_state_destroy(st)
             gpe.gpe_grid_destroy(grid)
         else:
