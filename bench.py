@@ -934,14 +934,22 @@ def run_extra(args):
             gpe.gpe_grid_destroy(grid)
         else:
             shells = inputs.batch_shells(args.shells)
+            dtype_id = BATCH_STATES[args.batch_state][0]
+
+            def shell_args(wl):
+                b = wl.box
+                return (gpe.make_box(b.nx, b.ny, b.nz, b.hx),
+                        gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes), wl.V_cut)
+
+            # brick shape from the batch autotuner (every shell, the batch
+            # kernels, 20 imaginary-time steps per candidate)
+            sa = [shell_args(wl) for wl in shells]
+            best, tuned = gpe.gpe_batch_autotune([x[0] for x in sa], [x[1] for x in sa], [x[2] for x in sa],
+                                                 dtype_id, 20)
+            brick = (best["bx"], best["by"], best["bz"])
             grids, states, cells = [], [], []
             for wl in shells:
-                b = wl.box
-                gb = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
-                pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
-                # 8x8x8 bricks: faster than 8x8x4 on these smaller, thicker shells
-                # (6.1e10 against 5.7e10 cell-steps/s)
-                g = gpe.gpe_grid_create_analytic(gb, pot, wl.V_cut, gpe.make_opts((8, 8, 8)))
+                g = gpe.gpe_grid_create_analytic(*shell_args(wl), gpe.make_opts(brick))
                 grids.append(g)
                 cells.append(gpe.gpe_grid_get_info(g).n_active)
             mine = gdist.shard(cells, world, rank)
@@ -985,9 +993,12 @@ def run_extra(args):
                                "dmu_median_quantiles": [float(np.quantile(med, q)) for q in (0, 0.5, 0.9, 1)],
                                "per_shell": floors},
                         max_steps=args.steps * STEPS_PER_BENCH, seconds=el, scaling="strong",
+                        brick=list(brick), autotune=[{"brick": [r["bx"], r["by"], r["bz"]],
+                                                      "ms_per_step": r["ms_per_step"],
+                                                      "cell_steps_per_s": r["cell_steps_per_s"]} for r in tuned],
                         config="seeded uneven ellipsoidal shells (radius U[0.5,1] x 360 cells, aspects U[0.7,1], "
                                "thickness U[4,10] cells, g U[100,3000]), one persistent launch, graph-replayed, "
-                               "8x8x8 bricks")
+                               "brick shape from the autotuner")
             gpe.gpe_batch_destroy(batch)
             for st in states:
                 gpe.gpe_state_destroy(st)

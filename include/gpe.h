@@ -539,8 +539,8 @@ typedef struct gpe_tune_result {
  * (staged; wavefront with 2-8 bricks per task; for GPE_TUNE_REAL also the RK4
  * stages fused in pairs, GPE_SCHED_PAIR, on 8x8x4 bricks) on the grid that
  * gpe_grid_create_analytic(box, pot, V_cut) builds, for `nsteps` real-time
- * (RK4) or imaginary-time steps of a state of type dtype, and return the
- * fastest in *best (use its fields in gpe_grid_opts).  all (room for 8
+ * (RK4) or imaginary-time steps of a state of type dtype (complex; real
+ * types for imaginary time only), and return the fastest in *best (use its fields in gpe_grid_opts).  all (room for 8
  * entries, may be NULL) receives every timing and *n_all their number.
  * Results are cached per device, state type, step kind and size class
  * (n_active within a factor sqrt(2)); with all == NULL a cached answer is
@@ -549,6 +549,23 @@ typedef struct gpe_tune_result {
 int gpe_autotune(const gpe_box *box, const gpe_potential *pot, double V_cut,
                  int dtype, int mode, int nsteps, gpe_tune_result *best,
                  gpe_tune_result *all, int *n_all, gpe_stream stream);
+
+/* The brick shape for a batch of shells (gpe_batch_create; the batch kernels
+ * run the staged schedule): for each candidate shape (8x8x8, 8x8x4, 8x4x4)
+ * builds the n grids gpe_grid_create_analytic(boxes[i], pots[i], V_cuts[i])
+ * makes, fills states of type dtype with a smooth test wavefunction, makes
+ * the batch and times `nsteps` imaginary-time steps of all shells (g = 1,
+ * N = 1, dt = 0.2 / (sum 2/h^2 + max V) per shell; the difference between
+ * runs of one and two graph-replayed blocks of nsteps steps, so set-up and
+ * copies cancel).  Returns the fastest in *best (cell_steps_per_s counts the
+ * active cells of every shell), every timing in all (room for 3 entries, may
+ * be NULL) and their number in *n_all.  Nothing is cached.  Synchronous;
+ * allocates temporary grids, states and batches.  GPE_ERR_ARG for n < 1,
+ * an unknown state type or nsteps < 1. */
+int gpe_batch_autotune(const gpe_box *boxes, const gpe_potential *pots,
+                       const double *V_cuts, int n, int dtype, int nsteps,
+                       gpe_tune_result *best, gpe_tune_result *all,
+                       int *n_all, gpe_stream stream);
 
 #ifdef __cplusplus
 }

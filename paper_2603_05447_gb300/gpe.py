@@ -171,6 +171,9 @@ _SIGS = {
     "gpe_batch_destroy": (C.c_int, [_P]),
     "gpe_autotune": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.c_double, C.c_int, C.c_int, C.c_int,
                                C.POINTER(gpe_tune_result), C.POINTER(gpe_tune_result), C.POINTER(C.c_int), _P]),
+    "gpe_batch_autotune": (C.c_int, [C.POINTER(gpe_box), C.POINTER(gpe_potential), C.POINTER(C.c_double), C.c_int,
+                                     C.c_int, C.c_int, C.POINTER(gpe_tune_result), C.POINTER(gpe_tune_result),
+                                     C.POINTER(C.c_int), _P]),
     "gpe_ramp_forward": (C.c_int, [_P, C.POINTER(gpe_real_params), C.c_int64, C.c_double, C.c_int, C.POINTER(_P), _P]),
     "gpe_ramp_backward": (C.c_int, [_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P]),
     "gpe_tape_destroy": (C.c_int, [_P]),
@@ -554,6 +557,22 @@ def gpe_autotune(box, pot, V_cut, dtype, mode, nsteps, timings=True, stream=None
     _check(load().gpe_autotune(C.byref(box), C.byref(pot), float(V_cut), int(dtype), int(mode), int(nsteps),
                                C.byref(best), allr if timings else None, C.byref(n), stream_handle(stream)))
     return best.asdict(), [allr[i].asdict() for i in range(n.value)]
+
+
+def gpe_batch_autotune(boxes, pots, V_cuts, dtype, nsteps, stream=None):
+    """Brick shape for a batch of shells: (best, every timing) as dicts."""
+    n = len(boxes)
+    if not (len(pots) == len(V_cuts) == n):
+        raise ValueError("boxes, pots and V_cuts must have the same length")
+    bx = (gpe_box * n)(*boxes)
+    px = (gpe_potential * n)(*pots)
+    vc = (C.c_double * n)(*[float(v) for v in V_cuts])
+    best = gpe_tune_result()
+    allr = (gpe_tune_result * 3)()
+    m = C.c_int()
+    _check(load().gpe_batch_autotune(bx, px, vc, n, int(dtype), int(nsteps), C.byref(best), allr, C.byref(m),
+                                     stream_handle(stream)))
+    return best.asdict(), [allr[i].asdict() for i in range(m.value)]
 
 
 def gpe_ramp_forward(state, params: gpe_real_params, nsteps, t0=0.0, K=64, stream=None):

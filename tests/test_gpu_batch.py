@@ -162,6 +162,52 @@ def test_batch_of_real_states_matches_the_complex_batch_and_the_solo_solver(real
             gpe.gpe_grid_destroy(g)
 
 
+@pytest.mark.parametrize("dtype", [gpe.GPE_C64, gpe.GPE_R32])
+def test_batch_autotune_times_every_brick_shape_on_the_batch(dtype):
+    """The batch tuner builds the shells in each brick shape, times the batch
+    and returns the fastest; the shape it picks builds a batch that runs."""
+    shells = [inputs.ShellWorkload(n=48, a_cells=18.0, g=500.0), inputs.ShellWorkload(n=64, a_cells=24.0, g=900.0),
+              inputs.ShellWorkload(n=40, a_cells=14.0, g=300.0)]
+    args = []
+    for wl in shells:
+        b = wl.box
+        args.append((gpe.make_box(b.nx, b.ny, b.nz, b.hx),
+                     gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes), wl.V_cut))
+    best, allr = gpe.gpe_batch_autotune([a[0] for a in args], [a[1] for a in args], [a[2] for a in args], dtype, 10)
+    assert sorted((r["bx"], r["by"], r["bz"]) for r in allr) == [(8, 4, 4), (8, 8, 4), (8, 8, 8)]
+    assert all(r["ms_per_step"] > 0 and r["cell_steps_per_s"] > 0 and r["sched"] == gpe.GPE_SCHED_STAGED for r in allr)
+    assert best["cell_steps_per_s"] == max(r["cell_steps_per_s"] for r in allr)
+    grids = [gpe.gpe_grid_create_analytic(*a, gpe.make_opts((best["bx"], best["by"], best["bz"]))) for a in args]
+    states = [gpe.gpe_state_create(g, dtype) for g in grids]
+    batch = None
+    try:
+        for g, st, wl in zip(grids, states, shells):
+            idx, i, j, k = gpe.packed_coords(g)
+            b = wl.box
+            npt = np.complex64 if dtype == gpe.GPE_C64 else np.float32
+            psi = np.zeros(gpe.gpe_grid_get_info(g).n_packed, npt)
+            psi[idx] = np.sqrt(np.maximum(wl.mu0 - wl.potential(b.x0 + i * b.hx, b.y0 + j * b.hy, b.z0 + k * b.hz),
+                                          0.0) / wl.g)
+            gpe.gpe_state_load(st, psi, gpe.GPE_LAYOUT_COMPACT)
+        batch = gpe.gpe_batch_create(states)
+        params = [gpe.gpe_imag_params(wl.g, wl.stable_dt() * 20, 1.0) for wl in shells]
+        rc, conv, steps, obs = gpe.gpe_batch_ground_state(batch, params, 1e-300, 5, 10, check=False)
+        assert steps == [10, 10, 10] and all(abs(o["norm"] - 1.0) < 1e-5 for o in obs)
+    finally:
+        if batch is not None:
+            gpe.gpe_batch_destroy(batch)
+        for st in states:
+            gpe.gpe_state_destroy(st)
+        for g in grids:
+            gpe.gpe_grid_destroy(g)
+    for bad in (dict(dtype=7), dict(nsteps=0)):
+        kw = dict(dtype=dtype, nsteps=10)
+        kw.update(bad)
+        with pytest.raises(gpe.GpeError) as e:
+            gpe.gpe_batch_autotune([args[0][0]], [args[0][1]], [args[0][2]], kw["dtype"], kw["nsteps"])
+        assert e.value.code == gpe.GPE_ERR_ARG
+
+
 def test_graph_replay_matches_eager_steps_bit_for_bit():
     case = ragged_shell()
     g1, eager = make(case)
