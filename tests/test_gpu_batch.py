@@ -285,6 +285,19 @@ def test_autotune_returns_a_timed_valid_layout():
     gpe.gpe_grid_destroy(grid)
 
 
+def test_autotune_takes_real_states_for_imaginary_time_only():
+    wl = inputs.SHELL_64
+    b = wl.box
+    box = gpe.make_box(b.nx, b.ny, b.nz, b.hx)
+    pot = gpe.make_potential(gpe.GPE_POT_ELLIPSOID_SHELL, wl.w, *wl.axes)
+    best, allr = gpe.gpe_autotune(box, pot, wl.V_cut, gpe.GPE_R32, gpe.GPE_TUNE_IMAG, 5)
+    assert len(allr) == 7 and best["cell_steps_per_s"] == max(r["cell_steps_per_s"] for r in allr)
+    assert all(r["ms_per_step"] > 0 for r in allr)
+    with pytest.raises(gpe.GpeError) as e:
+        gpe.gpe_autotune(box, pot, wl.V_cut, gpe.GPE_R32, gpe.GPE_TUNE_REAL, 5)
+    assert e.value.code == gpe.GPE_ERR_ARG
+
+
 def _c4_small_states(dtype):
     """Four seeded shells of the batch family (radius scale 40 cells instead
     of 360: boxes of 76-104 cells, 1e5-2.5e5 active), parabolic initial
