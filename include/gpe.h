@@ -351,7 +351,9 @@ int gpe_step_real(gpe_state *st, const gpe_real_params *p, int64_t nsteps,
                   double t0, gpe_stream stream);
 
 /* ------------------------------------------------------------------ observables */
-/* FP64 reductions over the active cells (products in the state's precision):
+/* FP64 reductions over the active cells (products in the state's precision,
+ * each 4-cell segment's terms summed in that precision, the segment sums
+ * accumulated in FP64 in a fixed order):
  *   norm   = sum |psi|^2 dV                           (Eq. (3))
  *   e_kin  = sum Re(conj(psi) T psi) dV
  *   e_pot  = sum V |psi|^2 dV,  V = (1 - s_blend) V0 + s_blend V1
