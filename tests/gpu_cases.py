@@ -82,3 +82,16 @@ def ramp_case():
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def tiny_box(nx, ny, nz, h=(0.3, 0.35, 0.4), seed=9):
+    """A box smaller than one brick in some or all dimensions (down to a
+    single cell), every cell active, anisotropic spacings, seeded complex
+    psi; for the degenerate layouts (bricks mostly outside the box)."""
+    box = inputs.Box(nx, ny, nz, *h)
+    V = inputs.dense_potential(box, inputs.Harmonic(1.0, 1.3, 0.8))
+    rng = np.random.default_rng(seed)
+    psi = (rng.normal(size=box.shape) + 1j * rng.normal(size=box.shape)).astype(np.complex128)
+    psi = inputs.normalise(psi, box.dV)
+    lam = 2 / box.hx ** 2 + 2 / box.hy ** 2 + 2 / box.hz ** 2 + float(V.max())
+    return Case(f"tiny{nx}x{ny}x{nz}", box, V, np.inf, psi, 2.0, 0.2 / lam)
