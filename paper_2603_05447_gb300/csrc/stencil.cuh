@@ -443,22 +443,22 @@ struct WarpSpace {
     __device__ __forceinline__ static int slot(int hx, int y, int z) { return hx + SX * ((y + 1) + TY * (z + 1)); }
     __device__ __forceinline__ static int h(int y, int z) { return NP == 19 ? (y + 1) + TY * (z + 1) : y + BY * z; }
     uint4 units[UPS][PSTR];
-    // x halos.  7-point: per row the 16-byte unit of the neighbour segment that
-    // holds the halo cell (cell 3 of the -x brick's last segment of the row,
-    // cell 0 of the +x brick's first), filled by cp.async like the tile; the
-    // 19-point stencil keeps single cells (also on its halo rows and planes).
-    static constexpr int XW = NP == 19 ? (int)sizeof(CT) : 16;
+    // x halos: per row (for the 19-point stencil also on the halo rows and
+    // planes) the 16-byte unit of the neighbour segment that holds the halo
+    // cell (cell 3 of the -x brick's last segment of the row, cell 0 of the
+    // +x brick's first), filled by cp.async like the tile.
+    static constexpr int XW = 16;
     alignas(16) unsigned char xlo_[XH * XW];  // x = -1
     alignas(16) unsigned char xhi_[XH * XW];  // x = BX
     __device__ __forceinline__ CT xm_cell(int h) const  // the cell at x = -1 of row h
     {
-        return reinterpret_cast<const CT *>(xlo_ + h * XW)[NP == 19 ? 0 : CPU_ - 1];
+        return reinterpret_cast<const CT *>(xlo_ + h * XW)[CPU_ - 1];
     }
     __device__ __forceinline__ CT xp_cell(int h) const  // the cell at x = BX of row h
     {
         return reinterpret_cast<const CT *>(xhi_ + h * XW)[0];
     }
-    __device__ __forceinline__ CT *xm_slot(int h) { return reinterpret_cast<CT *>(xlo_ + h * XW) + (NP == 19 ? 0 : CPU_ - 1); }
+    __device__ __forceinline__ CT *xm_slot(int h) { return reinterpret_cast<CT *>(xlo_ + h * XW) + (CPU_ - 1); }
     __device__ __forceinline__ CT *xp_slot(int h) { return reinterpret_cast<CT *>(xhi_ + h * XW); }
     alignas(16) BrickRec rec[NR];
 #if GPE_REC_AHEAD
@@ -704,15 +704,38 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
                    W::slot(hx, (e & 1) ? BY : -1, (e & 2) ? BZ : -1), t % LPS);
         }
     }
-    // -x / +x faces, 7-point, identity transform: per row one 16-byte unit
-    // (the one holding cell 3 of the -x brick's segment, or cell 0 of the +x
-    // brick's) by cp.async; absent segments give a zero unit
+    // -x / +x faces, identity transform: per row one 16-byte unit (the one
+    // holding cell 3 of the -x brick's segment, or cell 0 of the +x brick's)
+    // by cp.async; absent segments give a zero unit.  For the 19-point
+    // stencil also the halo rows and planes, from the xy-edge (records
+    // 7..10) and xz-edge (11..14) neighbours; the y-z corner rows, read by
+    // no stencil, are zero.
     if constexpr (NP != 19 && ASYNC) {
         for (int u = lane; u < 2 * BY * BZ; u += 32) {
             const int face = u / (BY * BZ), v_ = u % (BY * BZ);
             const int y = v_ % BY, z = v_ / BY;
             uint32_t j = 0;
             const bool ok = seg_index(ws.rec[1 + face], (face == 0 ? S::SX - 1 : 0) + S::SX * y + S::PLANE * z, j);
+            const char *g = reinterpret_cast<const char *>(src + (ok ? j : 0u)) + (face == 0 ? 16 * (W::UPS - 1) : 0);
+            cp_async16((face == 0 ? ws.xlo_ : ws.xhi_) + 16 * W::h(y, z), g, ok);
+        }
+    } else if constexpr (ASYNC) {
+        constexpr int HY = BY + 2, HZ = BZ + 2;
+        for (int u = lane; u < 2 * HY * HZ; u += 32) {
+            const int face = u / (HY * HZ), v_ = u % (HY * HZ);
+            const int y = v_ % HY - 1, z = v_ / HY - 1;
+            const bool yin = y >= 0 && y < BY, zin = z >= 0 && z < BZ;
+            int r = 1 + face, ys = y, zs = z;
+            if (!yin) {
+                r = 7 + face + (y == BY ? 2 : 0);
+                ys = y < 0 ? BY - 1 : 0;
+            } else if (!zin) {
+                r = 11 + face + (z == BZ ? 2 : 0);
+                zs = z < 0 ? BZ - 1 : 0;
+            }
+            uint32_t j = 0;
+            const bool ok = (yin || zin) &&
+                            seg_index(ws.rec[r], (face == 0 ? S::SX - 1 : 0) + S::SX * ys + S::PLANE * zs, j);
             const char *g = reinterpret_cast<const char *>(src + (ok ? j : 0u)) + (face == 0 ? 16 * (W::UPS - 1) : 0);
             cp_async16((face == 0 ? ws.xlo_ : ws.xhi_) + 16 * W::h(y, z), g, ok);
         }
