@@ -745,6 +745,9 @@ __device__ __forceinline__ void brick_apply(WarpSpace<CT, BX, BY, BZ, NP> &ws, c
     // from the xy-edge (records 7..10) and xz-edge (11..14) neighbours
     {
         constexpr int HY = NP == 19 ? BY + 2 : BY, HZ = NP == 19 ? BZ + 2 : BZ, O = NP == 19 ? 1 : 0;
+        // unrolled, so that a lane's loads are all issued before the first
+        // of them is waited for
+#pragma unroll
         for (int u = lane; u < 2 * HY * HZ; u += 32) {
             const int face = u / (HY * HZ), v_ = u % (HY * HZ);
             const int y = v_ % HY - O, z = v_ / HY - O;
