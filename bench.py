@@ -829,6 +829,15 @@ def ramp_traced(gpe, inputs, torch, nsteps=5000, every=500, n_overlap=5, nsteps_
                       "complex64 RK4; the configuration's 5e4 steps cut to the step counts stated"}
 
 
+def alg_roofline(cell_steps_per_s, alg_bytes, what):
+    """Algorithmic bytes per active cell-step x rate, over the measured copy
+    bandwidth (whole-run rate: includes launch gaps and reductions)."""
+    peak, kind = measured_peaks()
+    achieved = cell_steps_per_s * alg_bytes / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "alg_bytes_per_cell_step": alg_bytes, "alg_bytes": what, "peak_kind": kind}
+
+
 def run_extra(args):
     """Ramp (2048^3, ~1e8 active), adjoint (512^3) and batch workloads: one
     JSON line each, beside the headline line of the default run."""
@@ -898,6 +907,8 @@ def run_extra(args):
                             value=info.n_active * nsteps * world / (ms / 1e3), n_active=info.n_active,
                             n_packed=info.n_packed, steps=nsteps, ms_per_step=ms / nsteps, norm_after=o["norm"],
                             dt=dt, v_max=info.v_max,
+                            roofline=alg_roofline(info.n_active * nsteps / (ms / 1e3), 24.0,
+                                                  "read psi, V0, V1; write psi"),
                             config="2048^3 box, shell semi-axis 800 cells + harmonic core radius 0.24, g=5000, "
                                    "16 seeded monotone knots over the run")
             else:
@@ -987,6 +998,8 @@ def run_extra(args):
             line.update(metric=f"batched ground states: active-cell ITP steps/s ({BATCH_STATES[args.batch_state][2]}, "
                                "FP64 norms)", dtype=args.batch_state,
                         unit="cell-steps/s", value=done / el, shells=len(shells), n_active_total=int(sum(cells)),
+                        roofline=alg_roofline(done / el, 20.0 if args.batch_state == "c64" else 12.0,
+                                              "psi in and out, E in"),
                         converged=int(gdist.sum_over_ranks(sum(conv))), tol_dmu=args.tol,
                         floor={"checks": FLOOR_CHECKS, "every": 100,
                                "below_tol": int(np.sum(med < args.tol)),
